@@ -205,13 +205,14 @@ class Plan:
         nn = inf["n_nodes"]
         perm = np.zeros(len(self.traj), np.int64)
         ni = np.zeros(10 * nn, np.int64)
-        nd = np.zeros(7 * nn)
+        nd = np.zeros(11 * nn)
         sc = np.zeros(6)
         lib().hho_plan_export(self._h, _ptr(perm, _ip), _ptr(ni, _ip), _ptr(nd), _ptr(sc))
         ni = ni.reshape(nn, 10)
-        nd = nd.reshape(nn, 7)
+        nd = nd.reshape(nn, 11)
         return dict(perm=perm, level=ni[:, 0], depth=ni[:, 1], t=ni[:, 2], begin=ni[:, 3], end=ni[:, 4],
                     child0=ni[:, 5], nchild=ni[:, 6], N=ni[:, 7:10], rect=nd[:, :4], lo=nd[:, 4:7],
+                    eta=nd[:, 7:10], node_zbar=nd[:, 10],
                     zbar=sc[0], kmin=sc[1], kmax=sc[2], zh_floor=sc[3], zh_mid=sc[4], min_ext=sc[5],
                     **inf)
 

@@ -518,7 +518,10 @@ typedef struct {
     int t;           /* merges above this node (root: 0) */
     i64 begin, end;  /* member range in perm */
     double rect[4];  /* a, b, e, g after the minimum-extent rule */
+    double zbar;     /* design plane: mean member height */
+    double zmin, zmax; /* member height range */
     double lo[3];    /* lattice origin in (u, v, n) */
+    double eta[3];   /* lattice density (samples per unit) per axis */
     i64 N[3];        /* lattice sizes */
     i64 child0, nchild;
 } hho_node;
@@ -551,12 +554,71 @@ static int cmp_keyed(const void* A, const void* B) {
     return (a->idx < b->idx) ? -1 : (a->idx > b->idx);
 }
 
+/* Spectral extent of a subarray's compressed subimage.  Sec. III bounds the  */
+/* local spectrum of the SDC+LLT subimage by the unit box |kappa_d| <= pi      */
+/* (Eq. eq_llt_spcm_trans); the paper notes the bound loosens for the last     */
+/* levels, where subarrays are large.  Reading: measure it.  For probe points p */
+/* of D (corners, face centres, centre) and local spectral components           */
+/* K = 2k (p - p')/|p - p'| (Eq. eq_kxyz_posp) with p' on the subarray's border */
+/* (4 points per edge) at the lowest and highest member heights -- the paper   */
+/* ignores z' fluctuation (Sec. II-B), which small subarrays cannot -- and      */
+/* k in {k_min, k_max}, the                                                     */
+/* transformed frequency is kappa = J^-T (K - k_c) with J the Jacobian of       */
+/* (u, v, n) and k_c = (k5 + k7)/2 = grad Phi (Eq. eq_dp_kc).  rho_d is the     */
+/* largest |kappa_d| / pi, rounded up to a multiple of 1/64.                    */
+static void spectral_extent(const hho_plan* pl, const double rect[4], double zbar, double zlo, double zhi,
+                            double rho[3]) {
+    const double* G = pl->grid;
+    double xs[3] = {G[0], G[0] + 0.5 * G[3] * (G[6] - 1), G[0] + G[3] * (G[6] - 1)};
+    double ys[3] = {G[1], G[1] + 0.5 * G[4] * (G[7] - 1), G[1] + G[4] * (G[7] - 1)};
+    double zs[3] = {G[2], G[2] + 0.5 * G[5] * (G[8] - 1), G[2] + G[5] * (G[8] - 1)};
+    double a = rect[0], b = rect[1], e = rect[2], g = rect[3];
+    double bx[12], by[12];
+    for (int q = 0; q < 4; ++q) {
+        double s = q / 4.0;
+        bx[q] = a + s * (b - a); by[q] = e;           /* bottom edge */
+        bx[4 + q] = b; by[4 + q] = e + s * (g - e);   /* right edge */
+        bx[8 + q] = b - s * (b - a); by[8 + q] = g;   /* top edge */
+    }
+    double ex[16], ey[16];
+    for (int q = 0; q < 12; ++q) { ex[q] = bx[q]; ey[q] = by[q]; }
+    for (int q = 0; q < 4; ++q) { ex[12 + q] = a; ey[12 + q] = g - (q / 4.0) * (g - e); } /* left edge */
+    rho[0] = rho[1] = rho[2] = 1.0;
+    for (int ix = 0; ix < 3; ++ix)
+        for (int iy = 0; iy < 3; ++iy)
+            for (int iz = 0; iz < 3; ++iz) {
+                int mids = (ix == 1) + (iy == 1) + (iz == 1);
+                if (mids == 1) continue; /* corners (0), face centres (2), centre (3) */
+                double p[3] = {xs[ix], ys[iy], zs[iz]};
+                double kp[30];
+                hho_keypoints(rect, zbar, pl->kmin, pl->kmax, p, kp);
+                double kc[3], J[9];
+                for (int d = 0; d < 3; ++d) kc[d] = 0.5 * (kp[12 + d] + kp[18 + d]);
+                const double* Ts = kp + 21;
+                for (int d = 0; d < 3; ++d) { J[d] = -Ts[d]; J[3 + d] = -Ts[3 + d]; J[6 + d] = Ts[6 + d]; }
+                /* kappa solves J^T kappa = K - k_c */
+                double JT[9] = {J[0], J[3], J[6], J[1], J[4], J[7], J[2], J[5], J[8]};
+                for (int q = 0; q < 16; ++q)
+                    for (int kk = 0; kk < 4; ++kk) {
+                        double K[3];
+                        k0vec(ex[q], ey[q], p, (kk & 2) ? zhi : zlo, (kk & 1) ? pl->kmax : pl->kmin, K);
+                        double rhs[3] = {K[0] - kc[0], K[1] - kc[1], K[2] - kc[2]}, kap[3];
+                        if (!solve3(JT, rhs, kap)) continue;
+                        for (int d = 0; d < 3; ++d) {
+                            double r = fabs(kap[d]) / HHO_PI;
+                            if (r > rho[d]) rho[d] = r;
+                        }
+                    }
+            }
+    for (int d = 0; d < 3; ++d) rho[d] = ceil(rho[d] * 64.0) / 64.0;
+}
+
 /* Extremes of (u, v, n) over the box D.  Reading (the paper gives no rule):   */
 /* u grows with x and is monotone in h^2 = (y - y'_0)^2 + zh^2 on an x-face, so */
 /* its extremes lie on the x faces at y in {y_lo, y_hi, clamp(e), clamp(g)} and */
 /* z in {z_lo, z_hi}; likewise v.  n grows with zh and with r, and r is least   */
 /* at the clamped subarray centre and greatest at a box corner.                 */
-static void lattice_bbox(const hho_plan* pl, const double rect[4], double mn[3], double mx[3]) {
+static void lattice_bbox(const hho_plan* pl, const double rect[4], double zbar, double mn[3], double mx[3]) {
     const double* G = pl->grid;
     double xl = G[0], xh = G[0] + G[3] * (G[6] - 1), yl = G[1], yh = G[1] + G[4] * (G[7] - 1), zl = G[2],
            zhh = G[2] + G[5] * (G[8] - 1);
@@ -570,27 +632,27 @@ static void lattice_bbox(const hho_plan* pl, const double rect[4], double mn[3],
     for (int i = 0; i < 4; ++i)
         for (int k = 0; k < 2; ++k) {
             p[0] = xl; p[1] = yc[i]; p[2] = zc[k];
-            uvn_phi(rect, pl->zbar, pl->kmin, pl->kmax, p, w);
+            uvn_phi(rect, zbar, pl->kmin, pl->kmax, p, w);
             if (w[0] < mn[0]) mn[0] = w[0];
             p[0] = xh;
-            uvn_phi(rect, pl->zbar, pl->kmin, pl->kmax, p, w);
+            uvn_phi(rect, zbar, pl->kmin, pl->kmax, p, w);
             if (w[0] > mx[0]) mx[0] = w[0];
             p[0] = xcnd[i]; p[1] = yl;
-            uvn_phi(rect, pl->zbar, pl->kmin, pl->kmax, p, w);
+            uvn_phi(rect, zbar, pl->kmin, pl->kmax, p, w);
             if (w[1] < mn[1]) mn[1] = w[1];
             p[1] = yh;
-            uvn_phi(rect, pl->zbar, pl->kmin, pl->kmax, p, w);
+            uvn_phi(rect, zbar, pl->kmin, pl->kmax, p, w);
             if (w[1] > mx[1]) mx[1] = w[1];
         }
     p[0] = clampd(0.5 * (a + b), xl, xh);
     p[1] = clampd(0.5 * (e + g), yl, yh);
     p[2] = zl;
-    uvn_phi(rect, pl->zbar, pl->kmin, pl->kmax, p, w);
+    uvn_phi(rect, zbar, pl->kmin, pl->kmax, p, w);
     mn[2] = w[2];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
             p[0] = i ? xh : xl; p[1] = j ? yh : yl; p[2] = zhh;
-            uvn_phi(rect, pl->zbar, pl->kmin, pl->kmax, p, w);
+            uvn_phi(rect, zbar, pl->kmin, pl->kmax, p, w);
             if (w[2] > mx[2]) mx[2] = w[2];
         }
 }
@@ -638,16 +700,21 @@ hho_plan* hho_plan_create(const double* traj, i64 n_pos, const double* freqs, in
     }
     pl->kmin = 2 * HHO_PI * freqs[0] / HHO_C;
     pl->kmax = 2 * HHO_PI * freqs[n_f - 1] / HHO_C;
-    double zs = 0;
-    for (i64 i = 0; i < n_pos; ++i) zs += traj[3 * i + 2];
+    double zs = 0, ztop = -1e300;
+    for (i64 i = 0; i < n_pos; ++i) {
+        zs += traj[3 * i + 2];
+        if (traj[3 * i + 2] > ztop) ztop = traj[3 * i + 2];
+    }
     pl->zbar = zs / (double)n_pos;
-    double zlo = grid[2] - pl->zbar, zhi = grid[2] + grid[5] * (grid[8] - 1) - pl->zbar;
+    /* D must lie in front of every position; a sample point is feasible when  */
+    /* it lies at least zh_floor above its subarray's design plane (reading).   */
+    double zlo = grid[2] - ztop, zhi = grid[2] + grid[5] * (grid[8] - 1) - pl->zbar;
     if (!(zlo > 0)) {
         free(pl);
         return NULL;
     }
     pl->zh_floor = 0.1 * zlo;
-    pl->zh_mid = 0.5 * (zlo + zhi);
+    pl->zh_mid = 0.5 * (grid[2] - pl->zbar + zhi);
     /* minimum subarray extent (reading): half the shortest wavelength */
     pl->min_ext = 0.5 * HHO_C / freqs[n_f - 1];
 
@@ -715,13 +782,32 @@ hho_plan* hho_plan_create(const double* traj, i64 n_pos, const double* freqs, in
                 nd->child0 = pl->level_start[l - 1] + j * f;
                 nd->nchild = f;
             }
-            double a = 1e300, b = -1e300, e = 1e300, g = -1e300;
+            double a = 1e300, b = -1e300, e = 1e300, g = -1e300, zsum = 0;
+            nd->zmin = 1e300;
+            nd->zmax = -1e300;
             for (i64 q = nd->begin; q < nd->end; ++q) {
                 const double* pp = traj + 3 * pl->perm[q];
                 if (pp[0] < a) a = pp[0];
                 if (pp[0] > b) b = pp[0];
                 if (pp[1] < e) e = pp[1];
                 if (pp[1] > g) g = pp[1];
+                if (pp[2] < nd->zmin) nd->zmin = pp[2];
+                if (pp[2] > nd->zmax) nd->zmax = pp[2];
+            }
+            /* design plane of the subarray (reading): its members' mean height, */
+            /* summed in original index order                                      */
+            {
+                i64 cnt = nd->end - nd->begin;
+                i64* ids = (i64*)malloc(sizeof(i64) * cnt);
+                memcpy(ids, pl->perm + nd->begin, sizeof(i64) * cnt);
+                for (i64 q = 1; q < cnt; ++q) { /* insertion sort: small ranges are typical */
+                    i64 v = ids[q], r = q - 1;
+                    while (r >= 0 && ids[r] > v) { ids[r + 1] = ids[r]; --r; }
+                    ids[r + 1] = v;
+                }
+                for (i64 q = 0; q < cnt; ++q) zsum += traj[3 * ids[q] + 2];
+                free(ids);
+                nd->zbar = zsum / (double)cnt;
             }
             if (b - a < pl->min_ext) {
                 double c = 0.5 * (a + b);
@@ -735,13 +821,15 @@ hho_plan* hho_plan_create(const double* traj, i64 n_pos, const double* freqs, in
             }
             nd->rect[0] = a; nd->rect[1] = b; nd->rect[2] = e; nd->rect[3] = g;
             if (l < nl - 1) {
-                double mn[3], mx[3];
+                double mn[3], mx[3], rho[3];
                 i64 pad[3];
-                lattice_bbox(pl, nd->rect, mn, mx);
+                lattice_bbox(pl, nd->rect, nd->zbar, mn, mx);
                 node_padding(pl, nd->t, pad);
+                spectral_extent(pl, nd->rect, nd->zbar, nd->zmin, nd->zmax, rho);
                 for (int k = 0; k < 3; ++k) {
-                    nd->lo[k] = mn[k] - (double)pad[k] / eta;
-                    nd->N[k] = (i64)ceil((mx[k] - mn[k]) * eta) + 1 + 2 * pad[k];
+                    nd->eta[k] = eta * rho[k];
+                    nd->lo[k] = mn[k] - (double)pad[k] / nd->eta[k];
+                    nd->N[k] = (i64)ceil((mx[k] - mn[k]) * nd->eta[k]) + 1 + 2 * pad[k];
                 }
             }
         }
@@ -764,7 +852,7 @@ void hho_plan_info(const hho_plan* pl, i64* out) {
 }
 
 /* Export: perm[n_pos]; per node {level, depth, t, begin, end, child0, nchild, N0, N1, N2}
- * (int64 x 10) and {a, b, e, g, lo0, lo1, lo2} (double x 7); scalars {zbar, kmin, kmax,
+ * (int64 x 10) and {a, b, e, g, lo0, lo1, lo2, eta0, eta1, eta2, zbar} (double x 11); scalars {zbar, kmin, kmax,
  * zh_floor, zh_mid, min_ext}. */
 void hho_plan_export(const hho_plan* pl, i64* perm, i64* nodes_i, double* nodes_d, double* scal) {
     memcpy(perm, pl->perm, sizeof(i64) * pl->n_pos);
@@ -773,9 +861,11 @@ void hho_plan_export(const hho_plan* pl, i64* perm, i64* nodes_i, double* nodes_
         i64* I = nodes_i + 10 * k;
         I[0] = nd->level; I[1] = nd->depth; I[2] = nd->t; I[3] = nd->begin; I[4] = nd->end;
         I[5] = nd->child0; I[6] = nd->nchild; I[7] = nd->N[0]; I[8] = nd->N[1]; I[9] = nd->N[2];
-        double* F = nodes_d + 7 * k;
+        double* F = nodes_d + 11 * k;
         for (int q = 0; q < 4; ++q) F[q] = nd->rect[q];
         for (int q = 0; q < 3; ++q) F[4 + q] = nd->lo[q];
+        for (int q = 0; q < 3; ++q) F[7 + q] = nd->eta[q];
+        F[10] = nd->zbar;
     }
     scal[0] = pl->zbar; scal[1] = pl->kmin; scal[2] = pl->kmax;
     scal[3] = pl->zh_floor; scal[4] = pl->zh_mid; scal[5] = pl->min_ext;
@@ -806,9 +896,9 @@ static void lattice_target(const hho_plan* pl, const hho_node* nd, i64 lin, doub
     i64 in = lin % nd->N[2];
     i64 iv = (lin / nd->N[2]) % nd->N[1];
     i64 iu = lin / (nd->N[2] * nd->N[1]);
-    tgt[0] = nd->lo[0] + (double)iu / pl->eta;
-    tgt[1] = nd->lo[1] + (double)iv / pl->eta;
-    tgt[2] = nd->lo[2] + (double)in / pl->eta;
+    tgt[0] = nd->lo[0] + (double)iu / nd->eta[0];
+    tgt[1] = nd->lo[1] + (double)iv / nd->eta[1];
+    tgt[2] = nd->lo[2] + (double)in / nd->eta[2];
 }
 
 /* footprint of node c at point p: base indices and weights; returns 1 if inside */
@@ -821,12 +911,12 @@ typedef struct {
 
 static void make_footprint(const hho_plan* pl, const hho_node* c, const double p[3], footprint* F) {
     double w4[4];
-    uvn_phi(c->rect, pl->zbar, pl->kmin, pl->kmax, p, w4);
+    uvn_phi(c->rect, c->zbar, pl->kmin, pl->kmax, p, w4);
     F->phi = w4[3];
     int T = pl->taps, o0 = -(T / 2 - 1);
     F->inside = 1;
     for (int k = 0; k < 3; ++k) {
-        double f = (w4[k] - c->lo[k]) * pl->eta;
+        double f = (w4[k] - c->lo[k]) * c->eta[k];
         double fl = floor(f);
         F->base[k] = (i64)fl + o0;
         kernel_weights(&pl->K, f - fl, F->w[k]);
@@ -938,7 +1028,7 @@ int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* 
                 if (!D[k].need[li]) continue;
                 double tgt[3], p[3];
                 lattice_target(pl, nd, li, tgt);
-                if (!preimage(nd->rect, pl->zbar, pl->kmin, pl->kmax, pl->zh_floor, pl->zh_mid, tgt, p)) continue;
+                if (!preimage(nd->rect, nd->zbar, pl->kmin, pl->kmax, pl->zh_floor, pl->zh_mid, tgt, p)) continue;
                 for (i64 c = 0; c < nd->nchild; ++c) {
                     footprint F;
                     make_footprint(pl, &pl->nodes[nd->child0 + c], p, &F);
@@ -962,12 +1052,12 @@ int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* 
                 ++loc_need;
                 double tgt[3], p[3];
                 lattice_target(pl, nd, li, tgt);
-                if (!preimage(nd->rect, pl->zbar, pl->kmin, pl->kmax, pl->zh_floor, pl->zh_mid, tgt, p)) {
+                if (!preimage(nd->rect, nd->zbar, pl->kmin, pl->kmax, pl->zh_floor, pl->zh_mid, tgt, p)) {
                     ++loc_inf;
                     continue;
                 }
                 double w4[4];
-                uvn_phi(nd->rect, pl->zbar, pl->kmin, pl->kmax, p, w4);
+                uvn_phi(nd->rect, nd->zbar, pl->kmin, pl->kmax, p, w4);
                 double f[2] = {0, 0};
                 if (l == 0) {
                     bpa_rc_point(&P, pl->traj, pl->perm, nd->begin, nd->end, p, f);

@@ -1,0 +1,168 @@
+/*
+ * hhffbp.h -- C ABI of the GB300 HHFFBPA library.
+ *
+ * Fast factorized backprojection for near-range handheld SAR (HHFFBPA) and the
+ * direct backprojection it approximates, from "A Fast and Accurate 3-D
+ * Reconstruction Algorithm for Near-Range Microwave Imaging with Handheld
+ * Synthetic Aperture Radar".  All compute runs in hand-written CUDA kernels for
+ * sm_103a; the host side only validates, plans and launches.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns an int status, HH_OK (0) on success.
+ *   - Trajectory: host float64[n_pos][3] (x', y', z') in metres, copied by the call.
+ *   - Frequencies: host float64[n_f] in Hz, strictly increasing and equidistant
+ *     (relative tolerance 1e-9); k = 2 pi f / c with c = 299 792 458 m/s.
+ *   - Echo: complex64[n_pos][n_f] (interleaved re, im; row = position in
+ *     trajectory order), the monostatic samples s(p', k) of Sec. II-A, Eq. (1).
+ *   - Image: complex64[nz][ny][nx] (x fastest); voxel (a, b, c) is the point
+ *     (x0 + a dx, y0 + b dy, z0 + c dz).
+ *   - Echo and image pointers may be device pointers (used in place) or host
+ *     pointers (copied to/from device inside the call, on the call's stream);
+ *     page-locked host memory makes those copies asynchronous.
+ *   - cuda_stream: a cudaStream_t (NULL = legacy default stream).  Imaging calls
+ *     are asynchronous on that stream and enqueue no host synchronisation.
+ *   - The caller owns echo and image buffers; a plan owns its device workspace.
+ */
+#ifndef HHFFBP_H
+#define HHFFBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define HH_OK 0
+#define HH_ERR_ARG 1              /* null pointer, size <= 0, bad grid/config, D not in front of the aperture */
+#define HH_ERR_FREQ_NONUNIFORM 2  /* frequencies not equidistant/increasing */
+#define HH_ERR_OOM 3              /* device or host allocation failed */
+#define HH_ERR_CUDA 4             /* a CUDA call failed; see hh_last_cuda_error() */
+#define HH_ERR_PLAN_NONCONVERGED 5 /* reserved: preimage solver failure rate too high */
+#define HH_ERR_DEVICE_FLAG 6      /* a kernel raised an error counter (see hhffbp_plan_counters) */
+#define HH_ERR_UNIMPLEMENTED 7
+#define HH_ERR_HOST_ONLY 8        /* the plan was built with HH_FLAG_HOST_ONLY and holds no device state */
+
+/* ---- plan flags --------------------------------------------------------- */
+#define HH_FLAG_HOST_ONLY 1u      /* build tree and sampling grids on the host only (no CUDA calls) */
+
+/* Output grid D (Sec. V: the final image grid). */
+typedef struct {
+    double x0, y0, z0;  /* first voxel centre, metres */
+    double dx, dy, dz;  /* spacings, metres, > 0 */
+    int32_t nx, ny, nz; /* voxel counts, > 0 */
+} hh_grid;
+
+/* Algorithm configuration.  The paper leaves the factorisation depth, the
+ * interpolation kernel and the range oversampling open (Sec. IV); these fields
+ * choose them. */
+typedef struct {
+    int32_t leaf_size;    /* positions per level-1 subarray: the tree depth is the largest d with
+                             2^d * leaf_size <= n_pos (leaves hold leaf_size .. 2*leaf_size-1) */
+    int32_t merge_factor; /* 2: pairwise merges as in Sec. III; 4: two binary levels per merge */
+    float eta;            /* lattice density per (u, v, n) unit before the per-axis spectral-extent
+                             scaling, >= 1 (1 = the unity sampling rate of Sec. III) */
+    int32_t taps;         /* interpolation taps per axis: 4 or 6 */
+    int32_t range_os;     /* range oversampling: N_fft = next power of two >= range_os * n_f */
+    uint32_t flags;       /* HH_FLAG_* */
+} hh_config;
+
+/* Plan summary. */
+typedef struct {
+    int32_t n_levels;          /* materialised levels including the root (1 = no factorisation) */
+    int32_t depth_leaves;      /* binary depth of the leaves */
+    int64_t n_nodes;           /* materialised nodes including the root */
+    int64_t level_nodes[32];   /* nodes per level, leaves first */
+    int64_t level_samples[32]; /* lattice samples per level (the root: the grid's voxel count) */
+    int64_t workspace_bytes;   /* device bytes owned by the plan */
+    int64_t n_fft;             /* range FFT length */
+    int64_t gate_start;        /* first stored range bin */
+    int64_t gate_bins;         /* stored range bins per position */
+    double dR;                 /* range bin spacing pi / (N_fft dk), metres */
+    double kc;                 /* centre wavenumber (k_min + k_max) / 2, rad/m */
+} hh_plan_info;
+
+typedef struct hh_plan hh_plan;
+
+/* Defaults: leaf_size 32, merge_factor 4, eta 2, taps 6, range_os 16, flags 0. */
+int hhffbp_default_config(hh_config* cfg);
+
+/*
+ * hhffbp_plan -- build the subarray tree and the compressed sampling grids
+ * (Sec. IV-A: 2^(M-1) level-1 subarrays; uniform grids in (u, v, n) of
+ * Eq. eq_uvw_xyz per subarray), allocate the device workspace and upload the
+ * descriptors on cuda_stream.  May synchronise the stream.  The plan depends on
+ * the trajectory and is rebuilt per scan (Sec. III: no reusable
+ * precalculation).  *out receives the plan (NULL on error).
+ * Errors: HH_ERR_ARG, HH_ERR_FREQ_NONUNIFORM, HH_ERR_OOM, HH_ERR_CUDA.
+ */
+int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                const hh_config* cfg, void* cuda_stream, hh_plan** out);
+
+/* Release a plan and its device workspace (NULL is accepted). */
+int hhffbp_plan_destroy(hh_plan* plan);
+
+/* Fill *info from the plan. */
+int hhffbp_plan_info(const hh_plan* plan, hh_plan_info* info);
+
+/*
+ * hhffbp_plan_export -- copy the plan's tree and grid descriptors to host arrays
+ * (for comparison with an independent implementation).  Any pointer may be NULL.
+ *   perm[n_pos]         position index of each tree slot (members of a node are contiguous)
+ *   nodes_i[n_nodes][10] {level, depth, t, begin, end, child0, nchild, N_u, N_v, N_n}
+ *   nodes_d[n_nodes][11] {x'min, x'max, y'min, y'max, lo_u, lo_v, lo_n, eta_u, eta_v, eta_n, zbar}
+ * Nodes are ordered by level (leaves first, the root last).
+ */
+int hhffbp_plan_export(const hh_plan* plan, int64_t* perm, int64_t* nodes_i, double* nodes_d);
+
+/*
+ * hhffbp_form_image -- HHFFBPA image of one scan (Sec. IV-A, Fig. 4):
+ *   range compression (Eq. eq2_rangecompression), level-1 subimages by BPA on
+ *   each subarray's grid with spatial downconversion (Eqs. eq_sdc_mul,
+ *   eq_sdc_phi), then per level interpolation of the compressed child subimages
+ *   onto the parent grid, remodulation and coherent summation, and finally the
+ *   same onto the Cartesian voxels of D.  echo: complex64[n_pos][n_f];
+ *   image: complex64[nz][ny][nx] written in full.  Asynchronous on cuda_stream;
+ *   allocates nothing.
+ * Errors: HH_ERR_ARG (null), HH_ERR_HOST_ONLY, HH_ERR_CUDA.
+ */
+int hhffbp_form_image(const hh_plan* plan, const void* echo_c64, void* image_c64, void* cuda_stream);
+
+/*
+ * hhffbp_plan_counters -- synchronise the plan's last stream and read the device
+ * counters of the last form_image: out[0] exact-fallback evaluations, out[1]
+ * infeasible lattice samples, out[2] preimage solver failures, out[3] range
+ * lookups outside the stored gate (must be 0), out[4] other kernel errors (must
+ * be 0).  Returns HH_ERR_DEVICE_FLAG when out[3] or out[4] is non-zero.
+ */
+int hhffbp_plan_counters(const hh_plan* plan, int64_t out[8]);
+
+/*
+ * bpa_form_image -- direct time-domain backprojection on range-compressed data
+ * (Eqs. eq2_rangecompression and eq2_bpatimedomain):
+ *   f(p) = sum_i exp(+j 2 k_c R_i) [(1 - t) P_i[m0] + t P_i[m0 + 1]],
+ *   R_i = ||p - p'_i||, m0 = floor(R_i / dR), t = R_i / dR - m0,
+ * with P_i the centred zero-padded IFFT of s(p'_i, k) (N_fft from cfg->range_os).
+ * Only cfg->range_os is used.  Workspace (the range profiles) is allocated and
+ * freed stream-ordered on cuda_stream.  Asynchronous on cuda_stream.
+ * Errors: HH_ERR_ARG, HH_ERR_FREQ_NONUNIFORM, HH_ERR_OOM, HH_ERR_CUDA.
+ */
+int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                   const hh_config* cfg, const void* echo_c64, void* image_c64, void* cuda_stream);
+
+/*
+ * hhffbp_adjoint -- transpose of hhffbp_form_image (reprojection of an image to
+ * echoes).  Not built yet: returns HH_ERR_UNIMPLEMENTED.
+ */
+int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, void* cuda_stream);
+
+/* Human-readable status text (static string). */
+const char* hh_status_string(int status);
+
+/* Last CUDA error code recorded by the library in this thread (0 = none). */
+int hh_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHFFBP_H */

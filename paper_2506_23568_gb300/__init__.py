@@ -1,0 +1,261 @@
+"""GB300 HHFFBPA: fast factorized backprojection for near-range handheld SAR.
+
+Thin Python binding over the C ABI declared in include/hhffbp.h (ctypes).  It
+only marshals arguments: every step of imaging runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  If the
+library is missing, every imaging call raises -- there is no CPU fallback.
+
+    import paper_2506_23568_gb300 as hh
+    plan = hh.Plan(traj, freqs, grid)                      # grid: hh.Grid or synth.Grid
+    img = plan.form_image(echo)                            # echo: complex64 [n_pos][n_f] (cuda)
+    ref = hh.bpa_form_image(traj, freqs, grid, echo)       # direct BPA on the same grid
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Grid", "Config", "Plan", "bpa_form_image", "lib", "LibraryError", "status_string", "SYMBOLS"]
+
+HH_OK = 0
+HH_ERR_ARG = 1
+HH_ERR_FREQ_NONUNIFORM = 2
+HH_ERR_OOM = 3
+HH_ERR_CUDA = 4
+HH_ERR_PLAN_NONCONVERGED = 5
+HH_ERR_DEVICE_FLAG = 6
+HH_ERR_UNIMPLEMENTED = 7
+HH_ERR_HOST_ONLY = 8
+HH_FLAG_HOST_ONLY = 1
+
+# every symbol declared in include/hhffbp.h
+SYMBOLS = ["hhffbp_default_config", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
+           "hhffbp_form_image", "hhffbp_plan_counters", "bpa_form_image", "hhffbp_adjoint", "hh_status_string",
+           "hh_last_cuda_error"]
+
+
+class LibraryError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        if status == HH_ERR_CUDA and _lib is not None:
+            msg += f" (cudaError {_lib.hh_last_cuda_error()})"
+        super().__init__(f"{what}: {msg}" if what else msg)
+
+
+class hh_grid(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class hh_config(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("merge_factor", ctypes.c_int32), ("eta", ctypes.c_float),
+                ("taps", ctypes.c_int32), ("range_os", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class hh_plan_info(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("depth_leaves", ctypes.c_int32), ("n_nodes", ctypes.c_int64),
+                ("level_nodes", ctypes.c_int64 * 32), ("level_samples", ctypes.c_int64 * 32),
+                ("workspace_bytes", ctypes.c_int64), ("n_fft", ctypes.c_int64), ("gate_start", ctypes.c_int64),
+                ("gate_bins", ctypes.c_int64), ("dR", ctypes.c_double), ("kc", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib(build_if_needed=True):
+    """Load (building first when sources changed) the in-tree CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_needed and _build.needs_build():
+            _build.build()
+        if not os.path.exists(path):
+            raise LibraryError(HH_ERR_CUDA, f"CUDA library not built ({path})")
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, dp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    L.hhffbp_default_config.argtypes = [ctypes.POINTER(hh_config)]
+    L.hhffbp_plan.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
+                              ctypes.POINTER(hh_config), vp, ctypes.POINTER(vp)]
+    L.hhffbp_plan_destroy.argtypes = [vp]
+    L.hhffbp_plan_info.argtypes = [vp, ctypes.POINTER(hh_plan_info)]
+    L.hhffbp_plan_export.argtypes = [vp, i64p, i64p, dp]
+    L.hhffbp_form_image.argtypes = [vp, vp, vp, vp]
+    L.hhffbp_plan_counters.argtypes = [vp, i64p]
+    L.bpa_form_image.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
+                                 ctypes.POINTER(hh_config), vp, vp, vp]
+    L.hhffbp_adjoint.argtypes = [vp, vp, vp, vp]
+    L.hh_status_string.argtypes = [ctypes.c_int]
+    L.hh_status_string.restype = ctypes.c_char_p
+    L.hh_last_cuda_error.argtypes = []
+    for name in SYMBOLS:
+        f = getattr(L, name)
+        if name != "hh_status_string":
+            f.restype = ctypes.c_int
+
+
+def status_string(status):
+    return lib().hh_status_string(int(status)).decode()
+
+
+def _check(status, what):
+    if status != HH_OK:
+        raise LibraryError(status, what)
+
+
+class Grid(hh_grid):
+    """Output grid: voxel (a, b, c) at (x0 + a dx, y0 + b dy, z0 + c dz); image [nz][ny][nx]."""
+
+    @classmethod
+    def from_any(cls, g):
+        if isinstance(g, hh_grid):
+            return g
+        t = g.as_tuple() if hasattr(g, "as_tuple") else tuple(g)
+        return cls(*[float(v) for v in t[:6]], *[int(v) for v in t[6:]])
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def Config(**kw):
+    """hh_config with the library defaults, overridden by keyword."""
+    c = hh_config()
+    _check(lib().hhffbp_default_config(ctypes.byref(c)), "default_config")
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise TypeError(f"unknown config field {k}")
+        setattr(c, k, v)
+    return c
+
+
+def _f64(a):
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _buffer_ptr(t):
+    """Device or host data pointer of a contiguous complex64 tensor/array."""
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+class Plan:
+    """A trajectory-specific HHFFBPA plan (tree + compressed sampling grids + workspace)."""
+
+    def __init__(self, traj, freqs, grid, stream=None, host_only=False, **cfg):
+        self.traj = _f64(traj)
+        self.freqs = _f64(freqs)
+        self.grid = Grid.from_any(grid)
+        self.config = Config(**cfg)
+        if host_only:
+            self.config.flags |= HH_FLAG_HOST_ONLY
+        L = lib()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(0) if host_only else _stream_ptr(stream)
+        st = L.hhffbp_plan(self.traj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(self.traj),
+                           self.freqs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(self.freqs),
+                           ctypes.byref(self.grid), ctypes.byref(self.config), s, ctypes.byref(h))
+        _check(st, "hhffbp_plan")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hhffbp_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        i = hh_plan_info()
+        _check(lib().hhffbp_plan_info(self._h, ctypes.byref(i)), "plan_info")
+        nl = i.n_levels
+        return dict(n_levels=nl, depth_leaves=i.depth_leaves, n_nodes=i.n_nodes,
+                    level_nodes=list(i.level_nodes[:nl]), level_samples=list(i.level_samples[:nl]),
+                    workspace_bytes=i.workspace_bytes, n_fft=i.n_fft, gate_start=i.gate_start,
+                    gate_bins=i.gate_bins, dR=i.dR, kc=i.kc)
+
+    def export(self):
+        inf = self.info()
+        nn = inf["n_nodes"]
+        perm = np.zeros(len(self.traj), np.int64)
+        ni = np.zeros((nn, 10), np.int64)
+        nd = np.zeros((nn, 11))
+        _check(lib().hhffbp_plan_export(self._h, perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        ni.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        nd.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "plan_export")
+        ls = np.concatenate([[0], np.cumsum(inf["level_nodes"])])
+        return dict(perm=perm, level=ni[:, 0], depth=ni[:, 1], t=ni[:, 2], begin=ni[:, 3], end=ni[:, 4],
+                    child0=ni[:, 5], nchild=ni[:, 6], N=ni[:, 7:10], rect=nd[:, :4], lo=nd[:, 4:7],
+                    eta=nd[:, 7:10], node_zbar=nd[:, 10], level_start=ls, **inf)
+
+    def form_image(self, echo, out=None, stream=None):
+        """HHFFBPA image (complex64 [nz][ny][nx]) of echo (complex64 [n_pos][n_f]).
+
+        echo/out may be CUDA tensors (used in place) or host tensors/arrays (copied
+        inside the call).  Runs asynchronously on ``stream`` (default: torch's current)."""
+        import torch
+
+        if out is None:
+            dev = echo.device if hasattr(echo, "device") else torch.device("cpu")
+            out = torch.empty(self.grid.shape, dtype=torch.complex64, device=dev)
+        _check(lib().hhffbp_form_image(self._h, _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
+               "hhffbp_form_image")
+        return out
+
+    def counters(self):
+        """Synchronise and read the device counters of the last form_image."""
+        out = np.zeros(8, np.int64)
+        st = lib().hhffbp_plan_counters(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        c = dict(fallbacks=int(out[0]), infeasible=int(out[1]), newton_fail=int(out[2]), gate_miss=int(out[3]),
+                 errors=int(out[4]))
+        _check(st, f"plan_counters {c}")
+        return c
+
+    def adjoint(self, image, out=None, stream=None):
+        _check(lib().hhffbp_adjoint(self._h, _buffer_ptr(image), _buffer_ptr(image), _stream_ptr(stream)),
+               "hhffbp_adjoint")
+
+
+def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16):
+    """Direct BPA on range-compressed data (complex64 [nz][ny][nx])."""
+    import torch
+
+    t, f = _f64(traj), _f64(freqs)
+    g = Grid.from_any(grid)
+    cfg = Config(range_os=range_os)
+    if out is None:
+        dev = echo.device if hasattr(echo, "device") else torch.device("cpu")
+        out = torch.empty(g.shape, dtype=torch.complex64, device=dev)
+    _check(lib().bpa_form_image(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
+                                f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
+                                ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
+           "bpa_form_image")
+    return out

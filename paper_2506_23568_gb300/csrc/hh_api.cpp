@@ -1,0 +1,392 @@
+// C ABI of the HHFFBPA library: argument checks, device workspace, launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hh_internal.h"
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int fail_cuda(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA;
+}
+
+#define HH_CUDA(call)                              \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return fail_cuda(e_); \
+    } while (0)
+
+#define HH_LAUNCH(call)                                        \
+    do {                                                       \
+        int e_ = (call);                                       \
+        if (e_ != 0) return fail_cuda((cudaError_t)e_);        \
+    } while (0)
+
+// true when ptr is host memory (pageable or page-locked), false for device/managed memory
+bool is_host_pointer(const void* ptr) {
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear: unregistered host pointers report an error on some drivers
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    HH_CUDA(cudaMalloc(ptr, bytes));
+    p->workspace_bytes += (int64_t)bytes;
+    return HH_OK;
+}
+
+void free_device(hh_plan* p) {
+    void** bufs[] = {&p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
+                     &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage};
+    for (void** b : bufs)
+        if (*b) {
+            cudaFree(*b);
+            *b = nullptr;
+        }
+    for (void*& t : p->d_tiles)
+        if (t) {
+            cudaFree(t);
+            t = nullptr;
+        }
+}
+
+std::vector<hh::DNode> device_nodes(const hh_plan* p) {
+    std::vector<hh::DNode> out(p->nodes.size());
+    for (size_t i = 0; i < p->nodes.size(); ++i) {
+        const hh::HNode& h = p->nodes[i];
+        hh::DNode d{};
+        const double a = h.rect[0], b = h.rect[1], e = h.rect[2], g = h.rect[3];
+        d.cx = 0.5 * (a + b);
+        d.cy = 0.5 * (e + g);
+        d.cz = h.zbar;
+        d.hxd = 0.5 * (b - a);
+        d.hyd = 0.5 * (g - e);
+        d.hx = (float)d.hxd;
+        d.hy = (float)d.hyd;
+        d.C2 = (float)(4 * (b - a) * (b - a) + 4 * (g - e) * (g - e));
+        d.usat = (float)(p->kmax / hh::kPi * (b - a));
+        d.vsat = (float)(p->kmax / hh::kPi * (g - e));
+        for (int k = 0; k < 3; ++k) {
+            d.lo[k] = (float)h.lo[k];
+            d.eta[k] = (float)h.eta[k];
+            d.N[k] = (int32_t)h.N[k];
+        }
+        d.mem_begin = (int32_t)h.begin;
+        d.mem_end = (int32_t)h.end;
+        d.child0 = (int32_t)h.child0;
+        d.nchild = (int32_t)h.nchild;
+        d.pool_off = h.pool_off;
+        out[i] = d;
+    }
+    return out;
+}
+
+int upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    HH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return HH_OK;
+}
+
+#define HH_TRY(expr)            \
+    do {                        \
+        int r_ = (expr);        \
+        if (r_ != HH_OK) {      \
+            free_device(p);     \
+            delete p;           \
+            return r_;          \
+        }                       \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int hhffbp_default_config(hh_config* cfg) {
+    if (!cfg) return HH_ERR_ARG;
+    cfg->leaf_size = 32;
+    cfg->merge_factor = 4;
+    cfg->eta = 2.0f;
+    cfg->taps = 6;
+    cfg->range_os = 16;
+    cfg->flags = 0;
+    return HH_OK;
+}
+
+int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                const hh_config* cfg, void* cuda_stream, hh_plan** out) {
+    if (!out) return HH_ERR_ARG;
+    *out = nullptr;
+    int st = hh::validate_inputs(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, true);
+    if (st != HH_OK) return st;
+    hh_plan* p = new (std::nothrow) hh_plan();
+    if (!p) return HH_ERR_OOM;
+    p->n_pos = n_pos;
+    p->n_f = n_f;
+    p->grid = *grid;
+    p->cfg = *cfg;
+    p->traj.assign(traj_xyz, traj_xyz + 3 * n_pos);
+    p->freqs.assign(freqs_hz, freqs_hz + n_f);
+    HH_TRY(hh::build_host_plan(p));
+    for (const auto& nd : p->nodes)
+        for (int k = 0; k < 3; ++k)
+            if (nd.N[k] > INT32_MAX / 4) {
+                delete p;
+                return HH_ERR_ARG;
+            }
+    if (cfg->flags & HH_FLAG_HOST_ONLY) {
+        *out = p;
+        return HH_OK;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        g_last_cuda = (int)cudaGetLastError();
+        delete p;
+        return HH_ERR_CUDA;
+    }
+    std::vector<hh::DNode> dn = device_nodes(p);
+    std::vector<double> mem_pos(3 * (size_t)n_pos);
+    for (int64_t q = 0; q < n_pos; ++q)
+        for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
+    std::vector<float> tw = hh::twiddle_table(p->n_fft);
+    const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
+    HH_TRY(dev_alloc(p, &p->d_nodes, sizeof(hh::DNode) * dn.size()));
+    p->d_tiles.assign(p->n_levels, nullptr);
+    for (int l = 0; l < p->n_levels; ++l)
+        HH_TRY(dev_alloc(p, &p->d_tiles[l], sizeof(hh::DTile) * p->tiles[l].size()));
+    HH_TRY(dev_alloc(p, &p->d_mem_pos, sizeof(double) * mem_pos.size()));
+    HH_TRY(dev_alloc(p, &p->d_perm, sizeof(int64_t) * n_pos));
+    HH_TRY(dev_alloc(p, &p->d_prof, 8 * (size_t)n_pos * (size_t)p->gate_n));
+    if (p->max_pool > 0) {
+        HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
+        HH_TRY(dev_alloc(p, &p->d_pool[1], 8 * (size_t)p->max_pool));
+    }
+    HH_TRY(dev_alloc(p, &p->d_twiddle, sizeof(float) * tw.size()));
+    HH_TRY(dev_alloc(p, &p->d_wtable, sizeof(float) * p->wtable.size()));
+    HH_TRY(dev_alloc(p, &p->d_counters, sizeof(int64_t) * hh::CNT_N));
+    HH_TRY(dev_alloc(p, &p->d_echo_stage, 8 * (size_t)n_pos * (size_t)n_f));
+    HH_TRY(dev_alloc(p, &p->d_image_stage, 8 * (size_t)n_vox));
+    HH_TRY(upload(p->d_nodes, dn.data(), sizeof(hh::DNode) * dn.size(), s));
+    for (int l = 0; l < p->n_levels; ++l)
+        if (!p->tiles[l].empty())
+            HH_TRY(upload(p->d_tiles[l], p->tiles[l].data(), sizeof(hh::DTile) * p->tiles[l].size(), s));
+    HH_TRY(upload(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), s));
+    HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
+    HH_TRY(upload(p->d_twiddle, tw.data(), sizeof(float) * tw.size(), s));
+    HH_TRY(upload(p->d_wtable, p->wtable.data(), sizeof(float) * p->wtable.size(), s));
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_device(p);
+        delete p;
+        return fail_cuda(e);
+    }
+    p->on_device = true;
+    p->last_stream = cuda_stream;
+    *out = p;
+    return HH_OK;
+}
+
+int hhffbp_plan_destroy(hh_plan* plan) {
+    if (!plan) return HH_OK;
+    if (plan->on_device) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != plan->device) cudaSetDevice(plan->device);
+        cudaDeviceSynchronize();
+        free_device(plan);
+        if (cur != plan->device) cudaSetDevice(cur);
+    }
+    delete plan;
+    return HH_OK;
+}
+
+int hhffbp_plan_info(const hh_plan* p, hh_plan_info* info) {
+    if (!p || !info) return HH_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_levels = p->n_levels;
+    info->depth_leaves = p->depth_leaves;
+    info->n_nodes = (int64_t)p->nodes.size();
+    for (int l = 0; l < p->n_levels && l < 32; ++l) {
+        info->level_nodes[l] = p->level_start[l + 1] - p->level_start[l];
+        info->level_samples[l] = p->level_samples[l];
+    }
+    info->workspace_bytes = p->workspace_bytes;
+    info->n_fft = p->n_fft;
+    info->gate_start = p->gate0;
+    info->gate_bins = p->gate_n;
+    info->dR = p->dR;
+    info->kc = p->kc;
+    return HH_OK;
+}
+
+int hhffbp_plan_export(const hh_plan* p, int64_t* perm, int64_t* nodes_i, double* nodes_d) {
+    if (!p) return HH_ERR_ARG;
+    if (perm) std::memcpy(perm, p->perm.data(), sizeof(int64_t) * p->perm.size());
+    for (size_t k = 0; k < p->nodes.size(); ++k) {
+        const hh::HNode& n = p->nodes[k];
+        if (nodes_i) {
+            int64_t* I = nodes_i + 10 * k;
+            I[0] = n.level; I[1] = n.depth; I[2] = n.t; I[3] = n.begin; I[4] = n.end;
+            I[5] = n.child0; I[6] = n.nchild; I[7] = n.N[0]; I[8] = n.N[1]; I[9] = n.N[2];
+        }
+        if (nodes_d) {
+            double* F = nodes_d + 11 * k;
+            for (int q = 0; q < 4; ++q) F[q] = n.rect[q];
+            for (int q = 0; q < 3; ++q) F[4 + q] = n.lo[q];
+            for (int q = 0; q < 3; ++q) F[7 + q] = n.eta[q];
+            F[10] = n.zbar;
+        }
+    }
+    return HH_OK;
+}
+
+int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, void* cuda_stream) {
+    if (!cp || !echo_c64 || !image_c64) return HH_ERR_ARG;
+    if (!cp->on_device) return HH_ERR_HOST_ONLY;
+    hh_plan* p = const_cast<hh_plan*>(cp);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const int64_t n_vox = (int64_t)p->grid.nx * p->grid.ny * p->grid.nz;
+    const bool host_echo = is_host_pointer(echo_c64), host_img = is_host_pointer(image_c64);
+    const void* echo = echo_c64;
+    void* image = image_c64;
+    if (host_echo) {
+        HH_CUDA(cudaMemcpyAsync(p->d_echo_stage, echo_c64, 8 * (size_t)p->n_pos * p->n_f, cudaMemcpyHostToDevice, s));
+        echo = p->d_echo_stage;
+    }
+    if (host_img) image = p->d_image_stage;
+    HH_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int64_t) * hh::CNT_N, s));
+    const hh::KConst kc = hh::make_kconst(p);
+    HH_LAUNCH(hh::launch_rc(echo, static_cast<const int64_t*>(p->d_perm), p->n_pos, p->n_f, p->n_fft, p->gate0,
+                            p->gate_n, p->d_twiddle, p->d_prof, cuda_stream));
+    if (p->n_levels > 1) {
+        HH_LAUNCH(hh::launch_stage0(p, kc, cuda_stream));
+        for (int l = 1; l + 1 < p->n_levels; ++l) HH_LAUNCH(hh::launch_merge(p, kc, l, cuda_stream));
+    }
+    HH_LAUNCH(hh::launch_final(p, kc, image, cuda_stream));
+    if (host_img) HH_CUDA(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));
+    p->last_stream = cuda_stream;
+    return HH_OK;
+}
+
+int hhffbp_plan_counters(const hh_plan* p, int64_t out[8]) {
+    if (!p || !out) return HH_ERR_ARG;
+    std::memset(out, 0, sizeof(int64_t) * 8);
+    if (!p->on_device) return HH_ERR_HOST_ONLY;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(p->last_stream);
+    HH_CUDA(cudaStreamSynchronize(s));
+    HH_CUDA(cudaMemcpy(out, p->d_counters, sizeof(int64_t) * hh::CNT_N, cudaMemcpyDeviceToHost));
+    if (out[hh::CNT_GATE_MISS] != 0 || out[hh::CNT_ERROR] != 0) return HH_ERR_DEVICE_FLAG;
+    return HH_OK;
+}
+
+int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                   const hh_config* cfg, const void* echo_c64, void* image_c64, void* cuda_stream) {
+    int st = hh::validate_inputs(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, false);
+    if (st != HH_OK) return st;
+    if (!echo_c64 || !image_c64) return HH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    // range constants and a gate covering every (voxel, position) distance
+    hh_plan tmp;
+    tmp.n_pos = n_pos;
+    tmp.n_f = n_f;
+    tmp.grid = *grid;
+    tmp.cfg = *cfg;
+    hh::range_constants(freqs_hz, n_f, cfg->range_os, &tmp.kmin, &tmp.kmax, &tmp.kc, &tmp.dk, &tmp.n_fft, &tmp.dR);
+    double smin = 0, smax = 0;
+    const double lo[3] = {grid->x0, grid->y0, grid->z0};
+    const double hi[3] = {grid->x0 + grid->dx * (grid->nx - 1), grid->y0 + grid->dy * (grid->ny - 1),
+                          grid->z0 + grid->dz * (grid->nz - 1)};
+    for (int i = 0; i < 3; ++i) {
+        double tl = HUGE_VAL, th = -HUGE_VAL;
+        for (int64_t q = 0; q < n_pos; ++q) {
+            tl = std::fmin(tl, traj_xyz[3 * q + i]);
+            th = std::fmax(th, traj_xyz[3 * q + i]);
+        }
+        const double gap = std::fmax(0.0, std::fmax(lo[i] - th, tl - hi[i]));
+        const double span = std::fmax(std::fabs(hi[i] - tl), std::fabs(th - lo[i]));
+        smin += gap * gap;
+        smax += span * span;
+    }
+    tmp.gate0 = (int64_t)std::floor(std::sqrt(smin) / tmp.dR) - 2;
+    tmp.gate_n = (int64_t)std::ceil(std::sqrt(smax) / tmp.dR) + 3 - tmp.gate0;
+    tmp.gate_wrap = false;
+    if (tmp.gate_n >= tmp.n_fft) {
+        tmp.gate0 = 0;
+        tmp.gate_n = tmp.n_fft;
+        tmp.gate_wrap = true;
+    }
+    const hh::KConst kc = hh::make_kconst(&tmp);
+    std::vector<float> tw = hh::twiddle_table(tmp.n_fft);
+    const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
+    const bool host_echo = is_host_pointer(echo_c64), host_img = is_host_pointer(image_c64);
+    void *d_traj = nullptr, *d_prof = nullptr, *d_tw = nullptr, *d_cnt = nullptr, *d_echo = nullptr, *d_img = nullptr;
+    auto release = [&]() {
+        for (void* b : {d_traj, d_prof, d_tw, d_cnt, d_echo, d_img})
+            if (b) cudaFreeAsync(b, s);
+    };
+#define HH_STEP(call)                          \
+    do {                                       \
+        cudaError_t e_ = (cudaError_t)(call);  \
+        if (e_ != cudaSuccess) {               \
+            release();                         \
+            return fail_cuda(e_);              \
+        }                                      \
+    } while (0)
+    HH_STEP(cudaMallocAsync(&d_traj, sizeof(double) * 3 * n_pos, s));
+    HH_STEP(cudaMallocAsync(&d_prof, 8 * (size_t)n_pos * (size_t)tmp.gate_n, s));
+    HH_STEP(cudaMallocAsync(&d_tw, sizeof(float) * tw.size(), s));
+    HH_STEP(cudaMallocAsync(&d_cnt, sizeof(int64_t) * hh::CNT_N, s));
+    const void* echo = echo_c64;
+    void* image = image_c64;
+    if (host_echo) {
+        HH_STEP(cudaMallocAsync(&d_echo, 8 * (size_t)n_pos * n_f, s));
+        HH_STEP(cudaMemcpyAsync(d_echo, echo_c64, 8 * (size_t)n_pos * n_f, cudaMemcpyHostToDevice, s));
+        echo = d_echo;
+    }
+    if (host_img) {
+        HH_STEP(cudaMallocAsync(&d_img, 8 * (size_t)n_vox, s));
+        image = d_img;
+    }
+    HH_STEP(cudaMemcpyAsync(d_traj, traj_xyz, sizeof(double) * 3 * n_pos, cudaMemcpyHostToDevice, s));
+    HH_STEP(cudaMemcpyAsync(d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice, s));
+    HH_STEP(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * hh::CNT_N, s));
+    HH_STEP(hh::launch_rc(echo, nullptr, n_pos, n_f, tmp.n_fft, tmp.gate0, tmp.gate_n, d_tw, d_prof, cuda_stream));
+    HH_STEP(hh::launch_bpa(static_cast<const double*>(d_traj), n_pos, d_prof, kc, *grid, image, d_cnt, cuda_stream));
+    if (host_img) HH_STEP(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));
+    release();
+#undef HH_STEP
+    return HH_OK;
+}
+
+int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, void* cuda_stream) {
+    (void)plan; (void)image_c64; (void)echo_c64; (void)cuda_stream;
+    return HH_ERR_UNIMPLEMENTED;
+}
+
+const char* hh_status_string(int status) {
+    switch (status) {
+        case HH_OK: return "ok";
+        case HH_ERR_ARG: return "invalid argument";
+        case HH_ERR_FREQ_NONUNIFORM: return "frequencies are not equidistant and increasing";
+        case HH_ERR_OOM: return "out of memory";
+        case HH_ERR_CUDA: return "CUDA error";
+        case HH_ERR_PLAN_NONCONVERGED: return "preimage solver did not converge";
+        case HH_ERR_DEVICE_FLAG: return "a kernel raised an error counter";
+        case HH_ERR_UNIMPLEMENTED: return "not implemented";
+        case HH_ERR_HOST_ONLY: return "plan has no device state (built host-only)";
+        default: return "unknown status";
+    }
+}
+
+int hh_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Internal declarations shared by the host planner (hh_plan.cpp), the C ABI
+// (hh_api.cpp) and the kernels (hh_kernels.cu).  Plain-old-data only in the
+// structs that travel to the device.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/hhffbp.h"
+
+namespace hh {
+
+constexpr double kC = 299792458.0;  // m/s
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxLevels = 32;
+constexpr int kTableSteps = 1024;   // interpolation weight table: tau = j / kTableSteps
+
+// Device copy of a materialised node (every node of every level, root last).
+// Lattice sample (iu, iv, in) of a node sits at (u, v, n) = lo + (iu, iv, in) / eta
+// and is stored at pool[pool_off + (iu * N[1] + iv) * N[2] + in].
+struct DNode {
+    double cx, cy, cz;     // subarray centre ((a+b)/2, (e+g)/2) at the design height zbar
+    double hxd, hyd;       // half extents (b-a)/2, (g-e)/2 in FP64 (tile references)
+    float hx, hy;          // the same in FP32 (per-sample arithmetic)
+    float C2;              // 4 (b-a)^2 + 4 (g-e)^2
+    float usat, vsat;      // kmax/pi * (b-a), kmax/pi * (g-e): reach of u and v
+    float lo[3];           // lattice origin in (u, v, n)
+    float eta[3];          // lattice density per axis
+    int32_t N[3];          // lattice size per axis
+    int32_t mem_begin;     // tree-slot range of the members
+    int32_t mem_end;
+    int32_t child0;        // first child (node index), -1 for leaves
+    int32_t nchild;
+    int32_t pad_;
+    int64_t pool_off;      // first sample in the node's level pool
+};
+
+// Launch tiles: 8 x 8 x 4 lattice samples (u, v, n) of one node, or 8 x 8 x 4 voxels (x, y, z).
+constexpr int kTile0 = 8, kTile1 = 8, kTile2 = 4;
+// A launch tile: a box of lattice samples of one node, or a box of voxels.
+struct DTile {
+    int32_t node;
+    int32_t o0, o1, o2;    // first index per axis
+};
+
+// Host-side node record (the plan's own, FP64).
+struct HNode {
+    int level = 0, depth = 0, t = 0;
+    int64_t begin = 0, end = 0;
+    double rect[4] = {0, 0, 0, 0};  // x'min, x'max, y'min, y'max (after the minimum-extent rule)
+    double zbar = 0, zmin = 0, zmax = 0;
+    double lo[3] = {0, 0, 0}, eta[3] = {1, 1, 1};
+    int64_t N[3] = {0, 0, 0};
+    int64_t child0 = -1, nchild = 0;
+    int64_t pool_off = 0;
+};
+
+// Scalar constants handed to every kernel by value.
+struct KConst {
+    float kmin, kmax, kc;
+    float kmax_pi;         // kmax / pi
+    float kc_half;         // kc / 2
+    float kmax_quarter;    // kmax / 4
+    float kdiff_4pi;       // (kmax - kmin) / (4 pi)
+    float kmax_4pi;        // kmax / (4 pi)
+    float kmin_4pi;        // kmin / (4 pi)
+    float two_kc;          // 2 kc
+    float inv_dR;          // 1 / dR
+    float zh_floor;        // smallest height above a subarray's design plane for a lattice point
+    int32_t gate0;         // first stored range bin
+    int32_t gate_n;        // stored bins per position
+    int32_t wrap;          // 1 when the gate is the whole period (index modulo gate_n)
+    int32_t taps;
+    double kc_d, kmax_d, kmin_d;  // FP64 copies for tile references
+    double inv_dR_d;
+};
+
+// Device counters (int64): see hhffbp_plan_counters.
+enum Counter { CNT_FALLBACK = 0, CNT_INFEASIBLE = 1, CNT_NEWTON_FAIL = 2, CNT_GATE_MISS = 3, CNT_ERROR = 4,
+               CNT_N = 8 };
+
+}  // namespace hh
+
+struct hh_plan {
+    // inputs
+    int64_t n_pos = 0;
+    int32_t n_f = 0;
+    hh_grid grid{};
+    hh_config cfg{};
+    std::vector<double> traj, freqs;
+    // derived constants
+    double kmin = 0, kmax = 0, kc = 0, dk = 0, dR = 0, zbar_all = 0, zh_floor = 0;
+    int n_fft = 0;
+    int64_t gate0 = 0, gate_n = 0;
+    bool gate_wrap = false;
+    int depth_leaves = 0, n_levels = 0;
+    std::vector<int64_t> perm;
+    std::vector<hh::HNode> nodes;
+    std::vector<int64_t> level_start;        // n_levels + 1
+    std::vector<int64_t> level_samples;      // per level (root: voxel count)
+    std::vector<std::vector<hh::DTile>> tiles;  // per level (root: voxel tiles)
+    std::vector<float> wtable;               // (kTableSteps + 1) x taps
+    int64_t max_pool = 0;
+    // device state
+    bool on_device = false;
+    int device = 0;
+    void* d_nodes = nullptr;
+    std::vector<void*> d_tiles;
+    void* d_mem_pos = nullptr;   // double[n_pos][3], tree order
+    void* d_perm = nullptr;      // int64[n_pos]
+    void* d_prof = nullptr;      // float2[n_pos][gate_n], tree order
+    void* d_pool[2] = {nullptr, nullptr};
+    void* d_twiddle = nullptr;   // float2[2 n_fft]
+    void* d_wtable = nullptr;
+    void* d_counters = nullptr;  // int64[CNT_N]
+    void* d_echo_stage = nullptr;   // complex64[n_pos][n_f] for host echoes
+    void* d_image_stage = nullptr;  // complex64 image for host outputs
+    int64_t workspace_bytes = 0;
+    void* last_stream = nullptr;
+};
+
+namespace hh {
+
+// hh_plan.cpp
+int validate_inputs(const double* traj, int64_t n_pos, const double* freqs, int32_t n_f, const hh_grid* grid,
+                    const hh_config* cfg, bool need_plan);
+int build_host_plan(hh_plan* p);
+void range_constants(const double* freqs, int n_f, int range_os, double* kmin, double* kmax, double* kc,
+                     double* dk, int* n_fft, double* dR);
+std::vector<float> twiddle_table(int n_fft);
+std::vector<float> weight_table(int taps, double eta);
+
+// hh_kernels.cu (launch wrappers; return cudaError_t as int)
+int launch_rc(const void* echo, const int64_t* d_perm, int64_t n_pos, int n_f, int n_fft, int64_t gate0,
+              int64_t gate_n, const void* d_twiddle, void* d_prof, void* stream);
+int launch_bpa(const double* d_traj, int64_t n_pos, const void* d_prof, const KConst& kc, const hh_grid& g,
+               void* d_image, void* d_counters, void* stream);
+int launch_stage0(const hh_plan* p, const KConst& kc, void* stream);
+int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);
+int launch_final(const hh_plan* p, const KConst& kc, void* d_image, void* stream);
+KConst make_kconst(const hh_plan* p);
+
+}  // namespace hh

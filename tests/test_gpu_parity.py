@@ -1,0 +1,143 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: relative L2 error <= 1e-4 for the FP32 path (FP64 only in tile
+references), element by element on identical seeded inputs; the oracle uses
+its own plan.  HHFFBPA must also stay within -30 dB NRMSE of BPA.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def hh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_23568_gb300 as m
+
+    m.lib()
+    return m
+
+
+def _scene(name):
+    s = synth.CONFIGS[name]()
+    e = synth.scene_echo(s, device="cuda")
+    return s, e
+
+
+def _rel(gpu, ref):
+    return oracle.rel_l2(gpu.detach().cpu().numpy().astype(np.complex128).ravel(), np.asarray(ref).ravel())
+
+
+@pytest.mark.parametrize("name", ["small", "tiny"])
+def test_bpa_matches_oracle(hh, name):
+    s, e = _scene(name)
+    img = hh.bpa_form_image(s.traj, s.freqs, s.grid, e)
+    torch.cuda.synchronize()
+    ref = oracle.bpa_rc(s.traj, s.freqs, e.cpu().numpy(), s.grid.points()).reshape(s.grid.shape)
+    assert _rel(img, ref) < REL_TOL
+
+
+CFGS = [("small", dict(leaf_size=16)), ("small", dict(leaf_size=8, merge_factor=2, taps=4, eta=1.5)),
+        ("tiny", dict(leaf_size=32)), ("tiny", dict(leaf_size=64, taps=4))]
+
+
+@pytest.mark.parametrize("name,cfg", CFGS)
+def test_hhffbpa_matches_oracle(hh, name, cfg):
+    s, e = _scene(name)
+    plan = hh.Plan(s.traj, s.freqs, s.grid, **cfg)
+    img = plan.form_image(e)
+    cnt = plan.counters()
+    assert cnt["gate_miss"] == 0 and cnt["errors"] == 0
+    op = oracle.Plan(s.traj, s.freqs, s.grid, **cfg)
+    ref, st = op.hhffbpa(e.cpu().numpy())
+    ref = ref.reshape(s.grid.shape)
+    rel = _rel(img, ref)
+    assert rel < REL_TOL, (rel, cnt, st)
+    bpa = oracle.bpa_rc(s.traj, s.freqs, e.cpu().numpy(), s.grid.points()).reshape(s.grid.shape)
+    assert oracle.nrmse_db(img.cpu().numpy(), bpa) < -30
+
+
+def test_single_level_is_bpa(hh):
+    s, e = _scene("small")
+    plan = hh.Plan(s.traj, s.freqs, s.grid, leaf_size=10 ** 6)
+    assert plan.info()["n_levels"] == 1
+    img = plan.form_image(e)
+    ref = oracle.bpa_rc(s.traj, s.freqs, e.cpu().numpy(), s.grid.points()).reshape(s.grid.shape)
+    assert _rel(img, ref) < REL_TOL
+
+
+def test_host_buffers_match_device_buffers(hh):
+    s, e = _scene("small")
+    plan = hh.Plan(s.traj, s.freqs, s.grid, leaf_size=16)
+    dev = plan.form_image(e).cpu()
+    host_in = e.cpu().pin_memory()
+    host_out = torch.empty(s.grid.shape, dtype=torch.complex64).pin_memory()
+    plan.form_image(host_in, out=host_out)
+    torch.cuda.synchronize()
+    assert torch.equal(dev, host_out)
+    b_dev = hh.bpa_form_image(s.traj, s.freqs, s.grid, e).cpu()
+    b_host = hh.bpa_form_image(s.traj, s.freqs, s.grid, e.cpu())
+    torch.cuda.synchronize()
+    assert torch.equal(b_dev, b_host)
+
+
+def test_repeat_calls_are_deterministic(hh):
+    s, e = _scene("small")
+    plan = hh.Plan(s.traj, s.freqs, s.grid, leaf_size=16)
+    a = plan.form_image(e).clone()
+    b = plan.form_image(e)
+    assert torch.equal(a, b)
+
+
+def test_edge_single_voxel_and_thin_grid(hh):
+    s, e = _scene("small")
+    for g in [synth.Grid(0.001, -0.002, 0.19, 1e-3, 1e-3, 1e-2, 1, 1, 1),
+              synth.Grid(-0.03, 0.0, 0.18, 2e-3, 1e-3, 1e-2, 33, 1, 2)]:
+        plan = hh.Plan(s.traj, s.freqs, g, leaf_size=16)
+        img = plan.form_image(e)
+        ref, _ = oracle.Plan(s.traj, s.freqs, g, leaf_size=16).hhffbpa(e.cpu().numpy(), g.points())
+        assert _rel(img, ref.reshape(g.shape)) < REL_TOL
+        bref = oracle.bpa_rc(s.traj, s.freqs, e.cpu().numpy(), g.points()).reshape(g.shape)
+        assert _rel(hh.bpa_form_image(s.traj, s.freqs, g, e), bref) < REL_TOL
+
+
+def _clusters(grid, centres, half=(3, 3, 2)):
+    idx = []
+    for (a, b, c) in centres:
+        for dz in range(-half[2], half[2]):
+            for dy in range(-half[1], half[1]):
+                for dx in range(-half[0], half[0]):
+                    x, y, z = a + dx, b + dy, c + dz
+                    if 0 <= x < grid.nx and 0 <= y < grid.ny and 0 <= z < grid.nz:
+                        idx.append((z * grid.ny + y) * grid.nx + x)
+    return np.unique(np.array(idx))
+
+
+def test_mid_sampled_parity(hh):
+    """Full-size mid workload in the benchmark's launch configuration; the oracle
+    evaluates clustered voxel samples (demand-driven) and a few BPA voxels."""
+    s, e = _scene("mid")
+    g = s.grid
+    plan = hh.Plan(s.traj, s.freqs, g, leaf_size=64)
+    img = plan.form_image(e)
+    cnt = plan.counters()
+    ec = e.cpu().numpy()
+    idx = _clusters(g, [(128, 128, 32), (20, 230, 5), (250, 10, 60)])
+    ref, st = oracle.Plan(s.traj, s.freqs, g, leaf_size=64).hhffbpa(ec, g.points(idx))
+    got = img.reshape(-1)[torch.as_tensor(idx, device=img.device)].cpu().numpy()
+    assert oracle.rel_l2(got.astype(np.complex128), ref) < REL_TOL, (cnt, st)
+    bi = idx[::11]
+    bref = oracle.bpa_rc(s.traj, s.freqs, ec, g.points(bi))
+    bimg = hh.bpa_form_image(s.traj, s.freqs, g, e)
+    bgot = bimg.reshape(-1)[torch.as_tensor(bi, device=img.device)].cpu().numpy()
+    assert oracle.rel_l2(bgot.astype(np.complex128), bref) < REL_TOL
+    # accuracy of the fast method over the whole volume
+    assert oracle.nrmse_db(img.cpu().numpy(), bimg.cpu().numpy()) < -30

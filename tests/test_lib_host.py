@@ -1,0 +1,121 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol, and
+its host planning (tree, sampling grids) equals the oracle's independent plan.
+No compute call touches a GPU here (plans are built with HH_FLAG_HOST_ONLY)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_23568_gb300 as hh
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "hhffbp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = hh.lib()
+    declared = _declared_functions()
+    assert set(declared) == set(hh.SYMBOLS)
+    for name in declared:
+        assert isinstance(getattr(L, name), ctypes._CFuncPtr)
+
+
+def test_status_strings_and_defaults():
+    assert hh.status_string(hh.HH_OK) == "ok"
+    assert "not implemented" in hh.status_string(hh.HH_ERR_UNIMPLEMENTED)
+    c = hh.Config()
+    assert (c.leaf_size, c.merge_factor, c.taps, c.range_os) == (32, 4, 6, 16)
+    assert c.eta == pytest.approx(2.0)
+
+
+def _compare_plans(ge, oe):
+    for k in ["level", "depth", "t", "begin", "end", "nchild", "N"]:
+        np.testing.assert_array_equal(ge[k], oe[k], err_msg=k)
+    has = ge["nchild"] > 0
+    np.testing.assert_array_equal(ge["child0"][has], oe["child0"][has])
+    ls = ge["level_start"]
+    for k in range(ls[0], ls[-2]):  # every node's member set (order within a node is free)
+        assert set(ge["perm"][ge["begin"][k]:ge["end"][k]]) == set(oe["perm"][oe["begin"][k]:oe["end"][k]])
+    nonroot = slice(0, ls[-2])
+    np.testing.assert_allclose(ge["rect"], oe["rect"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(ge["node_zbar"], oe["node_zbar"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(ge["lo"][nonroot], oe["lo"][nonroot], rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(ge["eta"][nonroot], oe["eta"][nonroot])
+
+
+@pytest.mark.parametrize("name,cfg", [("tiny", dict(leaf_size=32)), ("small", dict(leaf_size=16)),
+                                      ("small", dict(leaf_size=8, merge_factor=2, taps=4, eta=1.5)),
+                                      ("mid", dict(leaf_size=64)), ("large", dict(leaf_size=64))])
+def test_host_plan_equals_oracle_plan(name, cfg):
+    s = synth.CONFIGS[name]()
+    ge = hh.Plan(s.traj, s.freqs, s.grid, host_only=True, **cfg).export()
+    oe = oracle.Plan(s.traj, s.freqs, s.grid, **cfg).export()
+    assert ge["n_levels"] == oe["n_levels"] and ge["depth_leaves"] == oe["depth_leaves"]
+    _compare_plans(ge, oe)
+
+
+def test_host_plan_ragged_position_count():
+    s = synth.small()
+    traj = s.traj[:229]  # not a power of two; leaves of 14 and 15 members
+    ge = hh.Plan(traj, s.freqs, s.grid, host_only=True, leaf_size=14).export()
+    oe = oracle.Plan(traj, s.freqs, s.grid, leaf_size=14).export()
+    sizes = ge["end"][:ge["level_start"][1]] - ge["begin"][:ge["level_start"][1]]
+    assert set(sizes.tolist()) <= {14, 15}
+    _compare_plans(ge, oe)
+
+
+def test_host_plan_single_level():
+    s = synth.small()
+    p = hh.Plan(s.traj, s.freqs, s.grid, host_only=True, leaf_size=10 ** 6)
+    assert p.info()["n_levels"] == 1
+
+
+def test_gate_covers_grid_ranges():
+    s = synth.tiny()
+    inf = hh.Plan(s.traj, s.freqs, s.grid, host_only=True).info()
+    pts = s.grid.points()[::97]
+    R = np.linalg.norm(pts[:, None, :] - s.traj[None, ::13, :], axis=2)
+    assert R.min() / inf["dR"] >= inf["gate_start"] and R.max() / inf["dR"] + 1 < inf["gate_start"] + inf["gate_bins"]
+
+
+@pytest.mark.parametrize("mutate,status", [
+    (lambda a: a.update(traj=a["traj"][:0]), hh.HH_ERR_ARG),
+    (lambda a: a.update(freqs=np.array([77e9])), hh.HH_ERR_ARG),
+    (lambda a: a.update(freqs=a["freqs"] * np.r_[1.0, np.ones(len(a["freqs"]) - 2) * 1.001, 1.0]),
+     hh.HH_ERR_FREQ_NONUNIFORM),
+    (lambda a: a.update(freqs=a["freqs"][::-1].copy()), hh.HH_ERR_FREQ_NONUNIFORM),
+    (lambda a: a.update(cfg=dict(taps=5)), hh.HH_ERR_ARG),
+    (lambda a: a.update(cfg=dict(merge_factor=3)), hh.HH_ERR_ARG),
+    (lambda a: a.update(cfg=dict(eta=0.5)), hh.HH_ERR_ARG),
+    (lambda a: a.update(cfg=dict(leaf_size=0)), hh.HH_ERR_ARG),
+    (lambda a: a.update(grid=synth.Grid(-0.01, -0.01, -0.5, 1e-3, 1e-3, 1e-2, 4, 4, 4)), hh.HH_ERR_ARG),
+    (lambda a: a.update(grid=synth.Grid(-0.01, -0.01, 0.2, 1e-3, 1e-3, 1e-2, 0, 4, 4)), hh.HH_ERR_ARG),
+    (lambda a: a.update(grid=synth.Grid(-0.01, -0.01, 0.2, -1e-3, 1e-3, 1e-2, 4, 4, 4)), hh.HH_ERR_ARG),
+])
+def test_plan_argument_errors(mutate, status):
+    s = synth.small()
+    a = dict(traj=s.traj, freqs=s.freqs, grid=s.grid, cfg={})
+    mutate(a)
+    with pytest.raises(hh.LibraryError) as ei:
+        hh.Plan(a["traj"], a["freqs"], a["grid"], host_only=True, **a["cfg"])
+    assert ei.value.status == status
+
+
+def test_host_only_plan_refuses_imaging():
+    s = synth.small()
+    p = hh.Plan(s.traj, s.freqs, s.grid, host_only=True)
+    L = hh.lib()
+    buf = np.zeros(16, np.complex64)
+    st = L.hhffbp_form_image(p._h, ctypes.c_void_p(buf.ctypes.data), ctypes.c_void_p(buf.ctypes.data), None)
+    assert st == hh.HH_ERR_HOST_ONLY
+    assert L.hhffbp_form_image(None, None, None, None) == hh.HH_ERR_ARG
+    assert L.hhffbp_adjoint(p._h, None, None, None) == hh.HH_ERR_UNIMPLEMENTED

@@ -133,9 +133,43 @@ int hhffbp_form_image(const hh_plan* plan, const void* echo_c64, void* image_c64
  * counters of the last form_image: out[0] exact-fallback evaluations, out[1]
  * infeasible lattice samples, out[2] preimage solver failures, out[3] range
  * lookups outside the stored gate (must be 0), out[4] other kernel errors (must
- * be 0).  Returns HH_ERR_DEVICE_FLAG when out[3] or out[4] is non-zero.
+ * be 0), out[5] position updates spent in exact fallbacks.  Returns HH_ERR_DEVICE_FLAG when out[3] or out[4] is non-zero.
  */
 int hhffbp_plan_counters(const hh_plan* plan, int64_t out[8]);
+
+/*
+ * hhffbp_plan_level_counts -- synchronise and return, for the last form_image,
+ * the number of lattice samples evaluated at each level (only the samples the
+ * image needs are evaluated; the last level is the voxel count), for
+ * min(max_levels, n_levels) levels, leaves first.  out[5] of
+ * hhffbp_plan_counters holds the member positions summed by exact fallbacks.
+ */
+int hhffbp_plan_level_counts(const hh_plan* plan, int64_t* evaluated, int32_t max_levels);
+
+/*
+ * hhffbp_plan_profile -- when enable != 0, hhffbp_form_image records a CUDA
+ * event on its stream before and after every stage (range compression, demand
+ * passes, level-1 subimages, each merge level, the final level, and the host
+ * copies), for hhffbp_plan_stage_times.  Costs one event record per stage.
+ */
+int hhffbp_plan_profile(hh_plan* plan, int enable);
+
+/*
+ * hhffbp_plan_stage_times -- synchronise and return the stage durations of the
+ * last profiled hhffbp_form_image: ms[i] (milliseconds), kind[i] (HH_STAGE_*)
+ * and level[i] (materialised level the stage works on, -1 when none), for
+ * i < *n_out <= max_n.  Any output pointer but n_out may be NULL.
+ */
+#define HH_STAGE_RC 0
+#define HH_STAGE_NEED_FINAL 1
+#define HH_STAGE_NEED_LEVEL 2
+#define HH_STAGE_LEAF 3
+#define HH_STAGE_MERGE 4
+#define HH_STAGE_FINAL 5
+#define HH_STAGE_H2D 6
+#define HH_STAGE_D2H 7
+int hhffbp_plan_stage_times(const hh_plan* plan, float* ms, int32_t* kind, int32_t* level, int32_t max_n,
+                            int32_t* n_out);
 
 /*
  * bpa_form_image -- direct time-domain backprojection on range-compressed data
@@ -149,6 +183,18 @@ int hhffbp_plan_counters(const hh_plan* plan, int64_t out[8]);
  */
 int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
                    const hh_config* cfg, const void* echo_c64, void* image_c64, void* cuda_stream);
+
+/*
+ * hhffbp_plan_preimages -- diagnostic: run the device preimage solver of the
+ * sampling grids (the xyz point whose (u, v, n) of Eq. eq_uvw_xyz equals a
+ * target; Sec. IV-A converts uniform (u, v, n) grids to xyz grids this way) on
+ * n host targets float64[n][3] of non-root node `node` (export order).  out:
+ * host float64[n][4] = absolute (x, y, z) and 1.0 when feasible (converged with
+ * height above the node's design plane >= the plan's floor), else 0.0.
+ * Allocates, and synchronises cuda_stream.
+ */
+int hhffbp_plan_preimages(const hh_plan* plan, int64_t node, const double* targets, int64_t n, double* out,
+                          void* cuda_stream);
 
 /*
  * hhffbp_adjoint -- transpose of hhffbp_form_image (reprojection of an image to

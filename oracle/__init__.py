@@ -70,6 +70,9 @@ def _declare(L):
     L.hho_uvn.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _i64, _dp]
     L.hho_preimage.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_double, _dp, _i64, _dp, _i32p]
+    L.hho_jacobian_ts.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]
+    L.hho_jacobian_s.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, _dp]
     L.hho_ls_weights.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _i64, _dp]
     L.hho_ls_weights.restype = ctypes.c_int
     L.hho_plan_create.argtypes = [_dp, _i64, _dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int,
@@ -166,6 +169,22 @@ def preimage(rect, zbar, kmin, kmax, zh_floor, zh_mid, targets):
     return xyz.reshape(-1, 3), ok.astype(bool)
 
 
+def jacobian_ts(rect, zbar, kmin, kmax, p):
+    """Jacobian of (u, v, n) in (x, y, z) from the key points: diag(-1, -1, 1) T_s."""
+    r, pp = _f64(rect), _f64(p)
+    out = np.zeros(9)
+    lib().hho_jacobian_ts(_ptr(r), zbar, kmin, kmax, _ptr(pp), _ptr(out))
+    return out.reshape(3, 3)
+
+
+def jacobian_s(rect, kmin, kmax, x, y, s):
+    """Jacobian of (u, v, n) in (x, y, s = zh^2) used by the preimage solver."""
+    r = _f64(rect)
+    out = np.zeros(9)
+    lib().hho_jacobian_s(_ptr(r), kmin, kmax, x, y, s, _ptr(out))
+    return out.reshape(3, 3)
+
+
 def ls_weights(taps, eta, tau):
     t = _f64(np.atleast_1d(tau))
     w = np.zeros(len(t) * taps)
@@ -223,13 +242,16 @@ class Plan:
         p = _f64(pts)
         e = _ri(echo)
         out = np.zeros(2 * len(p))
-        st = np.zeros(4, np.int64)
+        st = np.zeros(80, np.int64)
         rc = lib().hho_hhffbpa(self._h, _ptr(self.freqs), len(self.freqs), _ptr(e), _ptr(p), len(p), _ptr(out),
                                _ptr(st, _ip))
         if rc != 0:
             raise RuntimeError(f"oracle hhffbpa failed: {rc}")
+        nl = self.info()["n_levels"]
         return _cplx(out, (len(p),)), dict(fallbacks=int(st[0]), infeasible=int(st[1]), needed=int(st[2]),
-                                           leaf_updates=int(st[3]))
+                                           leaf_updates=int(st[3]), t_profiles=st[4] * 1e-9, t_topdown=st[5] * 1e-9,
+                                           t_final=st[7] * 1e-9, t_levels=(st[8:8 + nl] * 1e-9).tolist(),
+                                           needed_levels=st[40:40 + nl].tolist())
 
 
 def nrmse_db(x, ref):

@@ -18,8 +18,10 @@
  * Parity notes: functions marked "parity unpinned" have no value printed in the
  * paper to compare against; they are pinned only by invariants and limits.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdint.h>
+#include <time.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -30,6 +32,12 @@
 #define HHO_PI 3.14159265358979323846
 
 typedef int64_t i64;
+
+static double now_s(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 /* ------------------------------------------------------------------------ */
 /* small complex helpers (explicit, no complex.h)                            */
@@ -53,27 +61,48 @@ int hho_nfft(int n_f, int os_r) {
     return n;
 }
 
-static void dft_bin(const double* s_ri, int n_f, int n_fft, i64 m, double out[2]) {
+/* exp(+j pi q / n_fft) for q in [0, 2 n_fft) (tab may be NULL: computed per term) */
+static void dft_bin(const double* s_ri, int n_f, int n_fft, i64 m, const double* tab, double out[2]) {
     i64 mm = ((m % n_fft) + n_fft) % n_fft;
     i64 period = 2 * (i64)n_fft;
     double acc[2] = {0.0, 0.0};
     for (int n = 0; n < n_f; ++n) {
         i64 q = ((i64)(2 * n - n_f + 1) * mm) % period;
         if (q < 0) q += period;
-        double ang = HHO_PI * (double)q / (double)n_fft;
-        cmac(acc, s_ri[2 * n], s_ri[2 * n + 1], cos(ang), sin(ang));
+        double c, s;
+        if (tab) {
+            c = tab[2 * q];
+            s = tab[2 * q + 1];
+        } else {
+            double ang = HHO_PI * (double)q / (double)n_fft;
+            c = cos(ang);
+            s = sin(ang);
+        }
+        cmac(acc, s_ri[2 * n], s_ri[2 * n + 1], c, s);
     }
     out[0] = acc[0];
     out[1] = acc[1];
 }
 
+static double* twiddles(int n_fft) {
+    double* t = (double*)malloc(sizeof(double) * 4 * (size_t)n_fft);
+    for (i64 q = 0; q < 2 * (i64)n_fft; ++q) {
+        double ang = HHO_PI * (double)q / (double)n_fft;
+        t[2 * q] = cos(ang);
+        t[2 * q + 1] = sin(ang);
+    }
+    return t;
+}
+
 /* Profiles P_i[m] for m = m_lo .. m_lo + n_bins - 1 (mod N_fft), all positions. */
 void hho_rc_window(const double* echo_ri, i64 n_pos, int n_f, int n_fft, i64 m_lo, int n_bins,
                    double* prof_ri) {
+    double* tab = twiddles(n_fft);
 #pragma omp parallel for schedule(static)
     for (i64 i = 0; i < n_pos; ++i)
         for (int j = 0; j < n_bins; ++j)
-            dft_bin(echo_ri + 2 * i * n_f, n_f, n_fft, m_lo + j, prof_ri + 2 * (i * n_bins + j));
+            dft_bin(echo_ri + 2 * i * n_f, n_f, n_fft, m_lo + j, tab, prof_ri + 2 * (i * n_bins + j));
+    free(tab);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -144,7 +173,7 @@ static inline void prof_get(const hho_prof* P, i64 i, i64 m, double out[2]) {
         out[0] = P->win[2 * (i * P->n_bins + j)];
         out[1] = P->win[2 * (i * P->n_bins + j) + 1];
     } else {
-        dft_bin(P->echo_ri + 2 * i * P->n_f, P->n_f, P->n_fft, m, out);
+        dft_bin(P->echo_ri + 2 * i * P->n_f, P->n_f, P->n_fft, m, NULL, out);
     }
 }
 
@@ -340,16 +369,59 @@ static int solve3(const double A[9], const double rhs[3], double x[3]) {
 /* Preimage of a (u, v, n) target: the non-uniform xyz sampling point of a   */
 /* uniform (u, v, n) grid node (Sec. IV-A: grids "converted to non-uniform   */
 /* sampling grids in (x,y,z) through (eq_uvw_xyz)").  The paper gives no     */
-/* inverse; reading: the unique point with zh > 0 solving uvn(p) = target,   */
-/* found by damped Newton with the T_s Jacobian, started from the far-field  */
-/* direction-cosine estimate, with a homotopy from the subarray boresight as */
-/* the fallback.  A point is feasible when the solution exists with           */
-/* zh >= zh_floor.                                                            */
+/* inverse.  Reading: the unique point with zh > 0 solving uvn(p) = target.  */
+/* Every distance of Eq. eq_uvw_xyz depends on zh only through zh^2, so the  */
+/* solver works in (x, y, s = zh^2), where the map stays regular at the      */
+/* design plane (it folds there in zh) and s < 0 lies beyond the fold: damped */
+/* Newton with the analytic Jacobian from the far-field direction-cosine      */
+/* estimate, then a homotopy from the subarray boresight as the fallback.     */
+/* A point is feasible when the solution has zh >= zh_floor.                  */
 /* ------------------------------------------------------------------------ */
-static double resid_norm(const double rect[4], double zbar, double kmin, double kmax, const double p[3],
-                         const double tgt[3], double res[3]) {
-    double w[4];
-    uvn_phi(rect, zbar, kmin, kmax, p, w);
+static inline double dist_s(double x, double y, double s, double X, double Y) {
+    double q = (x - X) * (x - X) + (y - Y) * (y - Y) + s;
+    return sqrt(q > 1e-300 ? q : 1e-300);
+}
+
+/* (u, v, n) and their derivatives in (x, y, s) */
+static void uvn_s(const double rect[4], double kmin, double kmax, double x, double y, double s, double w[3],
+                  double* J) {
+    double a = rect[0], b = rect[1], e = rect[2], g = rect[3];
+    double x0 = clampd(x, a, b), y0 = clampd(y, e, g);
+    double da = dist_s(x, y, s, a, y0), db = dist_s(x, y, s, b, y0);
+    double de = dist_s(x, y, s, x0, e), dg = dist_s(x, y, s, x0, g);
+    double cx[4] = {a, a, b, b}, cy[4] = {e, g, e, g}, d[4], r = 0;
+    for (int j = 0; j < 4; ++j) {
+        d[j] = dist_s(x, y, s, cx[j], cy[j]);
+        r += d[j];
+    }
+    double C2 = 4 * (b - a) * (b - a) + 4 * (g - e) * (g - e);
+    double S = sqrt(r * r - C2 > 0 ? r * r - C2 : 0);
+    w[0] = kmax / HHO_PI * (da - db);
+    w[1] = kmax / HHO_PI * (de - dg);
+    w[2] = kmax / (4 * HHO_PI) * S - kmin / (4 * HHO_PI) * r;
+    if (!J) return;
+    /* y'_0 and x'_0 are constant where the clamp is active and cancel otherwise */
+    J[0] = kmax / HHO_PI * ((x - a) / da - (x - b) / db);
+    J[1] = kmax / HHO_PI * ((y - y0) / da - (y - y0) / db);
+    J[2] = kmax / HHO_PI * 0.5 * (1 / da - 1 / db);
+    J[3] = kmax / HHO_PI * ((x - x0) / de - (x - x0) / dg);
+    J[4] = kmax / HHO_PI * ((y - e) / de - (y - g) / dg);
+    J[5] = kmax / HHO_PI * 0.5 * (1 / de - 1 / dg);
+    double dn = (kmax * r / (S > 1e-300 ? S : 1e-300) - kmin) / (4 * HHO_PI), gx = 0, gy = 0, gs = 0;
+    for (int j = 0; j < 4; ++j) {
+        gx += (x - cx[j]) / d[j];
+        gy += (y - cy[j]) / d[j];
+        gs += 0.5 / d[j];
+    }
+    J[6] = dn * gx;
+    J[7] = dn * gy;
+    J[8] = dn * gs;
+}
+
+static double resid_s(const double rect[4], double kmin, double kmax, const double q[3], const double tgt[3],
+                      double res[3]) {
+    double w[3];
+    uvn_s(rect, kmin, kmax, q[0], q[1], q[2], w, NULL);
     double m = 0;
     for (int d = 0; d < 3; ++d) {
         res[d] = w[d] - tgt[d];
@@ -358,33 +430,26 @@ static double resid_norm(const double rect[4], double zbar, double kmin, double 
     return m;
 }
 
-static int newton(const double rect[4], double zbar, double kmin, double kmax, const double tgt[3], double p[3],
-                  int max_it, double tol) {
+static int newton_s(const double rect[4], double kmin, double kmax, const double tgt[3], double q[3], int max_it,
+                    double tol) {
     double res[3];
-    double rn = resid_norm(rect, zbar, kmin, kmax, p, tgt, res);
+    double rn = resid_s(rect, kmin, kmax, q, tgt, res);
     for (int it = 0; it < max_it; ++it) {
         if (rn <= tol) return 1;
-        double J[9], st[3];
-        uvn_jacobian(rect, zbar, kmin, kmax, p, J);
+        double J[9], st[3], w[3];
+        uvn_s(rect, kmin, kmax, q[0], q[1], q[2], w, J);
         if (!solve3(J, res, st)) return 0;
         double lam = 1.0;
         int accepted = 0;
         for (int bt = 0; bt < 40; ++bt) {
-            double q[3] = {p[0] - lam * st[0], p[1] - lam * st[1], p[2] - lam * st[2]};
-            if (q[2] - zbar > 0) {
-                double r2[3];
-                double rq = resid_norm(rect, zbar, kmin, kmax, q, tgt, r2);
-                if (rq < rn) {
-                    p[0] = q[0];
-                    p[1] = q[1];
-                    p[2] = q[2];
-                    rn = rq;
-                    res[0] = r2[0];
-                    res[1] = r2[1];
-                    res[2] = r2[2];
-                    accepted = 1;
-                    break;
-                }
+            double c[3] = {q[0] - lam * st[0], q[1] - lam * st[1], q[2] - lam * st[2]}, r2[3];
+            double rq = resid_s(rect, kmin, kmax, c, tgt, r2);
+            if (rq < rn) {
+                q[0] = c[0]; q[1] = c[1]; q[2] = c[2];
+                rn = rq;
+                res[0] = r2[0]; res[1] = r2[1]; res[2] = r2[2];
+                accepted = 1;
+                break;
             }
             lam *= 0.5;
         }
@@ -393,7 +458,7 @@ static int newton(const double rect[4], double zbar, double kmin, double kmax, c
     return rn <= tol;
 }
 
-/* returns 1 and p when feasible */
+/* returns 1 and p = (x, y, z) when feasible */
 static int preimage(const double rect[4], double zbar, double kmin, double kmax, double zh_floor, double zh_mid,
                     const double tgt[3], double p[3]) {
     const double tol = 1e-10;
@@ -412,27 +477,36 @@ static int preimage(const double rect[4], double zbar, double kmin, double kmax,
     double A = (kmax - kmin) / HHO_PI, Bq = kmax * C2 / (32 * HHO_PI);
     double R = (tgt[2] + sqrt(tgt[2] * tgt[2] + 4 * A * Bq)) / (2 * A);
     if (!(R > 1e-4)) R = 1e-4;
-    p[0] = xc + sx * R;
-    p[1] = yc + sy * R;
-    p[2] = zbar + R * sqrt(1 - s2);
-    int ok = newton(rect, zbar, kmin, kmax, tgt, p, 100, tol);
+    double q[3] = {xc + sx * R, yc + sy * R, R * R * (1 - s2)};
+    int ok = newton_s(rect, kmin, kmax, tgt, q, 100, tol);
     if (!ok) {
         /* homotopy from the boresight point at mid depth */
-        double q[3] = {xc, yc, zbar + zh_mid}, w0[4];
-        uvn_phi(rect, zbar, kmin, kmax, q, w0);
+        double w0[3];
+        q[0] = xc; q[1] = yc; q[2] = zh_mid * zh_mid;
+        uvn_s(rect, kmin, kmax, q[0], q[1], q[2], w0, NULL);
         ok = 1;
         for (int s = 1; s <= 32 && ok; ++s) {
             double lam = s / 32.0;
             double ts[3] = {w0[0] + lam * (tgt[0] - w0[0]), w0[1] + lam * (tgt[1] - w0[1]),
                             w0[2] + lam * (tgt[2] - w0[2])};
-            ok = newton(rect, zbar, kmin, kmax, ts, q, 60, s == 32 ? tol : 1e-7);
+            ok = newton_s(rect, kmin, kmax, ts, q, 60, s == 32 ? tol : 1e-7);
         }
-        p[0] = q[0];
-        p[1] = q[1];
-        p[2] = q[2];
     }
+    p[0] = q[0];
+    p[1] = q[1];
+    p[2] = zbar + sqrt(q[2] > 0 ? q[2] : 0);
     if (!ok) return 0;
-    return (p[2] - zbar) >= zh_floor;
+    return q[2] >= zh_floor * zh_floor;
+}
+
+/* Jacobians for tests: the key-point (T_s) Jacobian of (u, v, n) in (x, y, z) and the solver's in (x, y, s). */
+void hho_jacobian_ts(const double rect[4], double zbar, double kmin, double kmax, const double p[3], double* J) {
+    uvn_jacobian(rect, zbar, kmin, kmax, p, J);
+}
+
+void hho_jacobian_s(const double rect[4], double kmin, double kmax, double x, double y, double s, double* J) {
+    double w[3];
+    uvn_s(rect, kmin, kmax, x, y, s, w, J);
 }
 
 /* Batch preimage for tests: ok[i] = 1 when feasible. */
@@ -983,23 +1057,32 @@ static void child_contrib(const hho_plan* pl, const hho_prof* P, const hho_node*
     }
 }
 
-/* stats out: {fallbacks, infeasible needed samples, needed samples, leaf BPA updates} */
+/* stats out (int64[80]): {fallbacks, infeasible needed samples, needed samples, leaf BPA updates,
+ * t_profiles, t_topdown, t_leaves, t_final (ns), per-level time ns [8..40), per-level needed [40..72)} */
 int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* echo_ri, const double* pts,
                 i64 n_pts, double* out_ri, i64* stats) {
     int nl = pl->n_levels;
     const hho_node* root = &pl->nodes[pl->level_start[nl - 1]];
     i64 n_fallback = 0, n_infeasible = 0, n_needed = 0, n_updates = 0;
-    /* profiles: window over all positions covering the output points +/- 0.5 m */
+    i64 lvl_ns[32] = {0}, lvl_need[32] = {0};
+    double t0 = now_s();
+    /* profiles: window over all positions covering the output points +/- 0.3 m */
     double lo, hi;
     range_bounds(pl->traj, pl->n_pos, pts, n_pts, &lo, &hi);
     hho_prof P;
-    prof_init(&P, echo_ri, pl->n_pos, freqs, n_f, pl->os_r, lo - 0.5, hi + 0.5);
+    prof_init(&P, echo_ri, pl->n_pos, freqs, n_f, pl->os_r, lo - 0.3, hi + 0.3);
+    double t_prof = now_s() - t0;
 
     if (nl == 1) { /* no factorisation: M = 1, plain BPA-RC on the grid */
 #pragma omp parallel for schedule(dynamic, 16)
         for (i64 q = 0; q < n_pts; ++q) bpa_rc_point(&P, pl->traj, pl->perm, 0, pl->n_pos, pts + 3 * q, out_ri + 2 * q);
         prof_free(&P);
-        if (stats) { stats[0] = 0; stats[1] = 0; stats[2] = 0; stats[3] = pl->n_pos * n_pts; }
+        if (stats) {
+            memset(stats, 0, sizeof(i64) * 80);
+            stats[3] = pl->n_pos * n_pts;
+            stats[4] = (i64)(1e9 * t_prof);
+            stats[7] = (i64)(1e9 * (now_s() - t0 - t_prof));
+        }
         return 0;
     }
 
@@ -1008,6 +1091,12 @@ int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* 
         const hho_node* nd = &pl->nodes[k];
         D[k].need = (uint8_t*)calloc((size_t)(nd->N[0] * nd->N[1] * nd->N[2]), 1);
     }
+    if (getenv("HHO_MARK_ALL")) /* diagnostic: evaluate every lattice point */
+        for (i64 k = 0; k < pl->level_start[nl - 1]; ++k) {
+            const hho_node* nd = &pl->nodes[k];
+            memset(D[k].need, 1, (size_t)(nd->N[0] * nd->N[1] * nd->N[2]));
+        }
+    double t1 = now_s();
     /* top-down: mark what the output points need in the root's children */
     for (i64 c = 0; c < root->nchild; ++c) {
         const hho_node* cn = &pl->nodes[root->child0 + c];
@@ -1037,8 +1126,10 @@ int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* 
             }
         }
     }
+    double t_top = now_s() - t1;
     /* bottom-up values */
     for (int l = 0; l <= nl - 2; ++l) {
+        double tl0 = now_s();
         for (i64 k = pl->level_start[l]; k < pl->level_start[l + 1]; ++k) {
             const hho_node* nd = &pl->nodes[k];
             i64 NN = nd->N[0] * nd->N[1] * nd->N[2];
@@ -1077,13 +1168,16 @@ int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* 
             n_needed += loc_need;
             n_infeasible += loc_inf;
             n_updates += loc_upd;
+            lvl_need[l] += loc_need;
         }
+        lvl_ns[l] = (i64)(1e9 * (now_s() - tl0));
         if (l > 0)
             for (i64 k = pl->level_start[l - 1]; k < pl->level_start[l]; ++k) {
                 free(D[k].val);
                 D[k].val = NULL;
             }
     }
+    double tf0 = now_s();
     /* final: Cartesian voxels */
 #pragma omp parallel for schedule(dynamic, 64)
     for (i64 q = 0; q < n_pts; ++q) {
@@ -1104,10 +1198,19 @@ int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* 
     free(D);
     prof_free(&P);
     if (stats) {
+        memset(stats, 0, sizeof(i64) * 80);
         stats[0] = n_fallback;
         stats[1] = n_infeasible;
         stats[2] = n_needed;
         stats[3] = n_updates;
+        stats[4] = (i64)(1e9 * t_prof);
+        stats[5] = (i64)(1e9 * t_top);
+        stats[6] = lvl_ns[0];
+        stats[7] = (i64)(1e9 * (now_s() - tf0));
+        for (int l = 0; l < nl && l < 32; ++l) {
+            stats[8 + l] = lvl_ns[l];
+            stats[40 + l] = lvl_need[l];
+        }
     }
     return 0;
 }

@@ -34,8 +34,11 @@ HH_FLAG_HOST_ONLY = 1
 
 # every symbol declared in include/hhffbp.h
 SYMBOLS = ["hhffbp_default_config", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
-           "hhffbp_form_image", "hhffbp_plan_counters", "bpa_form_image", "hhffbp_adjoint", "hh_status_string",
-           "hh_last_cuda_error"]
+           "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
+           "hhffbp_plan_stage_times", "hhffbp_plan_preimages",
+           "bpa_form_image", "hhffbp_adjoint", "hh_status_string", "hh_last_cuda_error"]
+STAGE_NAMES = {0: "range_compression", 1: "need_final", 2: "need_level", 3: "leaf_subimages", 4: "merge",
+               5: "final", 6: "h2d", 7: "d2h"}
 
 
 class LibraryError(RuntimeError):
@@ -93,6 +96,11 @@ def _declare(L):
     L.hhffbp_plan_export.argtypes = [vp, i64p, i64p, dp]
     L.hhffbp_form_image.argtypes = [vp, vp, vp, vp]
     L.hhffbp_plan_counters.argtypes = [vp, i64p]
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.hhffbp_plan_level_counts.argtypes = [vp, i64p, ctypes.c_int32]
+    L.hhffbp_plan_preimages.argtypes = [vp, ctypes.c_int64, dp, ctypes.c_int64, dp, vp]
+    L.hhffbp_plan_profile.argtypes = [vp, ctypes.c_int]
+    L.hhffbp_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32p, i32p, ctypes.c_int32, i32p]
     L.bpa_form_image.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
                                  ctypes.POINTER(hh_config), vp, vp, vp]
     L.hhffbp_adjoint.argtypes = [vp, vp, vp, vp]
@@ -235,9 +243,39 @@ class Plan:
         out = np.zeros(8, np.int64)
         st = lib().hhffbp_plan_counters(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
         c = dict(fallbacks=int(out[0]), infeasible=int(out[1]), newton_fail=int(out[2]), gate_miss=int(out[3]),
-                 errors=int(out[4]))
+                 errors=int(out[4]), fallback_updates=int(out[5]))
         _check(st, f"plan_counters {c}")
         return c
+
+    def preimages(self, node, targets, stream=None):
+        """Device preimage solver on (u, v, n) targets of a node: (xyz float64[n][3], feasible bool[n])."""
+        t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros((len(t), 4))
+        _check(lib().hhffbp_plan_preimages(self._h, int(node), t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           len(t), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           _stream_ptr(stream)), "plan_preimages")
+        return out[:, :3], out[:, 3] > 0.5
+
+    def level_counts(self):
+        """Samples evaluated per level in the last form_image (synchronises)."""
+        out = np.zeros(32, np.int64)
+        _check(lib().hhffbp_plan_level_counts(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 32),
+               "plan_level_counts")
+        return out[:self.info()["n_levels"]].tolist()
+
+    def profile(self, enable=True):
+        """Record CUDA events between the stages of each form_image."""
+        _check(lib().hhffbp_plan_profile(self._h, int(bool(enable))), "plan_profile")
+
+    def stage_times(self):
+        """[(stage name, level, ms)] of the last profiled form_image (synchronises)."""
+        n = 64
+        ms = (ctypes.c_float * n)()
+        kind = (ctypes.c_int32 * n)()
+        lev = (ctypes.c_int32 * n)()
+        got = ctypes.c_int32()
+        _check(lib().hhffbp_plan_stage_times(self._h, ms, kind, lev, n, ctypes.byref(got)), "plan_stage_times")
+        return [(STAGE_NAMES.get(kind[i], str(kind[i])), int(lev[i]), float(ms[i])) for i in range(got.value)]
 
     def adjoint(self, image, out=None, stream=None):
         _check(lib().hhffbp_adjoint(self._h, _buffer_ptr(image), _buffer_ptr(image), _stream_ptr(stream)),

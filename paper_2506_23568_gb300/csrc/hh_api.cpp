@@ -48,7 +48,8 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
-                     &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage};
+                     &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
+                     &p->d_need, &p->d_xyz};
     for (void** b : bufs)
         if (*b) {
             cudaFree(*b);
@@ -59,7 +60,36 @@ void free_device(hh_plan* p) {
             cudaFree(t);
             t = nullptr;
         }
+    for (void*& ev : p->events)
+        if (ev) {
+            cudaEventDestroy(static_cast<cudaEvent_t>(ev));
+            ev = nullptr;
+        }
 }
+
+// Stage profiling: event i marks the start of stage i (and the end of stage i - 1).
+struct StageMarks {
+    hh_plan* p;
+    cudaStream_t s;
+    int n = 0;
+    int mark(int kind, int level) {
+        if (!p->profile) return HH_OK;
+        if ((int)p->events.size() <= n) {
+            cudaEvent_t ev;
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return fail_cuda(e);
+            p->events.push_back(ev);
+        }
+        cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(p->events[n]), s);
+        if (e != cudaSuccess) return fail_cuda(e);
+        if (kind >= 0) {
+            p->stage_kind.push_back(kind);
+            p->stage_level.push_back(level);
+        }
+        ++n;
+        return HH_OK;
+    }
+};
 
 std::vector<hh::DNode> device_nodes(const hh_plan* p) {
     std::vector<hh::DNode> out(p->nodes.size());
@@ -170,6 +200,8 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
         HH_TRY(dev_alloc(p, &p->d_pool[1], 8 * (size_t)p->max_pool));
     }
+    if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, (size_t)p->need_total));
+    if (p->xyz_total > 0) HH_TRY(dev_alloc(p, &p->d_xyz, 16 * (size_t)p->xyz_total));
     HH_TRY(dev_alloc(p, &p->d_twiddle, sizeof(float) * tw.size()));
     HH_TRY(dev_alloc(p, &p->d_wtable, sizeof(float) * p->wtable.size()));
     HH_TRY(dev_alloc(p, &p->d_counters, sizeof(int64_t) * hh::CNT_N));
@@ -258,22 +290,81 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
     const bool host_echo = is_host_pointer(echo_c64), host_img = is_host_pointer(image_c64);
     const void* echo = echo_c64;
     void* image = image_c64;
+    StageMarks sm{p, s};
+    p->stage_kind.clear();
+    p->stage_level.clear();
+#define HH_MARK(kind, level)                  \
+    do {                                      \
+        int r_ = sm.mark((kind), (level));    \
+        if (r_ != HH_OK) return r_;           \
+    } while (0)
     if (host_echo) {
+        HH_MARK(HH_STAGE_H2D, -1);
         HH_CUDA(cudaMemcpyAsync(p->d_echo_stage, echo_c64, 8 * (size_t)p->n_pos * p->n_f, cudaMemcpyHostToDevice, s));
         echo = p->d_echo_stage;
     }
     if (host_img) image = p->d_image_stage;
+    HH_MARK(HH_STAGE_RC, -1);
     HH_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int64_t) * hh::CNT_N, s));
     const hh::KConst kc = hh::make_kconst(p);
     HH_LAUNCH(hh::launch_rc(echo, static_cast<const int64_t*>(p->d_perm), p->n_pos, p->n_f, p->n_fft, p->gate0,
                             p->gate_n, p->d_twiddle, p->d_prof, cuda_stream));
     if (p->n_levels > 1) {
+        // top-down: which lattice samples the image needs (the footprints of needed points)
+        HH_MARK(HH_STAGE_NEED_FINAL, p->n_levels - 1);
+        HH_CUDA(cudaMemsetAsync(p->d_need, 0, (size_t)p->need_total, s));
+        HH_LAUNCH(hh::launch_need_final(p, kc, cuda_stream));
+        for (int l = p->n_levels - 2; l >= 1; --l) {
+            HH_MARK(HH_STAGE_NEED_LEVEL, l);
+            HH_LAUNCH(hh::launch_need_level(p, kc, l, cuda_stream));
+        }
+        // bottom-up: values at the needed samples
+        HH_MARK(HH_STAGE_LEAF, 0);
         HH_LAUNCH(hh::launch_stage0(p, kc, cuda_stream));
-        for (int l = 1; l + 1 < p->n_levels; ++l) HH_LAUNCH(hh::launch_merge(p, kc, l, cuda_stream));
+        for (int l = 1; l + 1 < p->n_levels; ++l) {
+            HH_MARK(HH_STAGE_MERGE, l);
+            HH_LAUNCH(hh::launch_merge(p, kc, l, cuda_stream));
+        }
     }
+    HH_MARK(HH_STAGE_FINAL, p->n_levels - 1);
     HH_LAUNCH(hh::launch_final(p, kc, image, cuda_stream));
-    if (host_img) HH_CUDA(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));
+    if (host_img) {
+        HH_MARK(HH_STAGE_D2H, -1);
+        HH_CUDA(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));
+    }
+    HH_MARK(-1, -1);
+#undef HH_MARK
     p->last_stream = cuda_stream;
+    return HH_OK;
+}
+
+int hhffbp_plan_profile(hh_plan* p, int enable) {
+    if (!p) return HH_ERR_ARG;
+    if (!p->on_device) return HH_ERR_HOST_ONLY;
+    p->profile = enable != 0;
+    return HH_OK;
+}
+
+int hhffbp_plan_stage_times(const hh_plan* p, float* ms, int32_t* kind, int32_t* level, int32_t max_n,
+                            int32_t* n_out) {
+    if (!p || !n_out || max_n < 0) return HH_ERR_ARG;
+    *n_out = 0;
+    if (!p->on_device) return HH_ERR_HOST_ONLY;
+    const int n = (int)p->stage_kind.size();
+    if (n == 0) return HH_OK;
+    HH_CUDA(cudaEventSynchronize(static_cast<cudaEvent_t>(p->events[n])));
+    const int m = n < max_n ? n : max_n;
+    for (int i = 0; i < m; ++i) {
+        if (ms) {
+            float t = 0.f;
+            HH_CUDA(cudaEventElapsedTime(&t, static_cast<cudaEvent_t>(p->events[i]),
+                                         static_cast<cudaEvent_t>(p->events[i + 1])));
+            ms[i] = t;
+        }
+        if (kind) kind[i] = p->stage_kind[i];
+        if (level) level[i] = p->stage_level[i];
+    }
+    *n_out = m;
     return HH_OK;
 }
 
@@ -281,10 +372,23 @@ int hhffbp_plan_counters(const hh_plan* p, int64_t out[8]) {
     if (!p || !out) return HH_ERR_ARG;
     std::memset(out, 0, sizeof(int64_t) * 8);
     if (!p->on_device) return HH_ERR_HOST_ONLY;
+    int64_t all[hh::CNT_N];
     cudaStream_t s = reinterpret_cast<cudaStream_t>(p->last_stream);
     HH_CUDA(cudaStreamSynchronize(s));
-    HH_CUDA(cudaMemcpy(out, p->d_counters, sizeof(int64_t) * hh::CNT_N, cudaMemcpyDeviceToHost));
+    HH_CUDA(cudaMemcpy(all, p->d_counters, sizeof(int64_t) * hh::CNT_N, cudaMemcpyDeviceToHost));
+    std::memcpy(out, all, sizeof(int64_t) * 8);
     if (out[hh::CNT_GATE_MISS] != 0 || out[hh::CNT_ERROR] != 0) return HH_ERR_DEVICE_FLAG;
+    return HH_OK;
+}
+
+int hhffbp_plan_level_counts(const hh_plan* p, int64_t* evaluated, int32_t max_levels) {
+    if (!p || !evaluated || max_levels < 0) return HH_ERR_ARG;
+    if (!p->on_device) return HH_ERR_HOST_ONLY;
+    int64_t all[hh::CNT_N];
+    HH_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(p->last_stream)));
+    HH_CUDA(cudaMemcpy(all, p->d_counters, sizeof(int64_t) * hh::CNT_N, cudaMemcpyDeviceToHost));
+    for (int l = 0; l < max_levels && l < p->n_levels; ++l)
+        evaluated[l] = (l == p->n_levels - 1) ? p->level_samples[l] : all[hh::CNT_NEEDED + l];
     return HH_OK;
 }
 
@@ -365,6 +469,27 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
     release();
 #undef HH_STEP
     return HH_OK;
+}
+
+int hhffbp_plan_preimages(const hh_plan* p, int64_t node, const double* targets, int64_t n, double* out,
+                          void* cuda_stream) {
+    if (!p || !targets || !out || n < 0) return HH_ERR_ARG;
+    if (!p->on_device) return HH_ERR_HOST_ONLY;
+    if (node < 0 || node >= p->level_start[p->n_levels - 1]) return HH_ERR_ARG;  // non-root nodes only
+    if (n == 0) return HH_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    void *d_t = nullptr, *d_o = nullptr;
+    cudaError_t e = cudaMalloc(&d_t, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_o, sizeof(double) * 4 * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, targets, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = (cudaError_t)hh::launch_preimage_probe(p, hh::make_kconst(p), (int)node, static_cast<const double*>(d_t), n,
+                                                   static_cast<double*>(d_o), cuda_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_o, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_t);
+    cudaFree(d_o);
+    return e == cudaSuccess ? HH_OK : fail_cuda(e);
 }
 
 int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, void* cuda_stream) {

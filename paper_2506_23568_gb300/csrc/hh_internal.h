@@ -76,8 +76,9 @@ struct KConst {
 };
 
 // Device counters (int64): see hhffbp_plan_counters.
+// CNT_NEEDED + level: samples evaluated at that level (the root: voxels).
 enum Counter { CNT_FALLBACK = 0, CNT_INFEASIBLE = 1, CNT_NEWTON_FAIL = 2, CNT_GATE_MISS = 3, CNT_ERROR = 4,
-               CNT_N = 8 };
+               CNT_FALLBACK_UPDATES = 5, CNT_NEEDED = 8, CNT_N = 8 + kMaxLevels };
 
 }  // namespace hh
 
@@ -113,10 +114,19 @@ struct hh_plan {
     void* d_twiddle = nullptr;   // float2[2 n_fft]
     void* d_wtable = nullptr;
     void* d_counters = nullptr;  // int64[CNT_N]
+    void* d_need = nullptr;      // uint8 per lattice sample of every non-root level (need_base offsets)
+    void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
+    std::vector<int64_t> need_base;  // per level: first sample in d_need
+    std::vector<int64_t> xyz_base;   // per level: first sample in d_xyz (levels >= 1)
+    int64_t need_total = 0, xyz_total = 0;
     void* d_echo_stage = nullptr;   // complex64[n_pos][n_f] for host echoes
     void* d_image_stage = nullptr;  // complex64 image for host outputs
     int64_t workspace_bytes = 0;
     void* last_stream = nullptr;
+    // stage profiling (hhffbp_plan_profile)
+    bool profile = false;
+    std::vector<void*> events;          // cudaEvent_t, created on demand
+    std::vector<int> stage_kind, stage_level;
 };
 
 namespace hh {
@@ -135,9 +145,13 @@ int launch_rc(const void* echo, const int64_t* d_perm, int64_t n_pos, int n_f, i
               int64_t gate_n, const void* d_twiddle, void* d_prof, void* stream);
 int launch_bpa(const double* d_traj, int64_t n_pos, const void* d_prof, const KConst& kc, const hh_grid& g,
                void* d_image, void* d_counters, void* stream);
+int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);
+int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_stage0(const hh_plan* p, const KConst& kc, void* stream);
 int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_final(const hh_plan* p, const KConst& kc, void* d_image, void* stream);
+int launch_preimage_probe(const hh_plan* p, const KConst& kc, int node, const double* d_tgt, int64_t n, double* d_out,
+                          void* stream);
 KConst make_kconst(const hh_plan* p);
 
 }  // namespace hh

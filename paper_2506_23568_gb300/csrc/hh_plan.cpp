@@ -393,6 +393,17 @@ int build_host_plan(hh_plan* p) {
         p->max_pool = std::max(p->max_pool, off);
     }
     p->level_samples[p->n_levels - 1] = (int64_t)p->grid.nx * p->grid.ny * p->grid.nz;
+    p->need_base.assign(p->n_levels, 0);
+    p->xyz_base.assign(p->n_levels, 0);
+    p->need_total = p->xyz_total = 0;
+    for (int l = 0; l + 1 < p->n_levels; ++l) {
+        p->need_base[l] = p->need_total;
+        p->need_total += p->level_samples[l];
+        if (l >= 1) {
+            p->xyz_base[l] = p->xyz_total;
+            p->xyz_total += p->level_samples[l];
+        }
+    }
 
     // ---- range gate: bins covering every range a kernel can look up.  For a
     // lattice of n in [n_lo, n_hi], the corner-distance sum r obeys

@@ -206,6 +206,17 @@ def test_local_spectrum_inside_unit_box_for_small_subarray():
     assert 0.9 < worst < 1.02
 
 
+def test_solver_jacobian_is_llt_matrix_in_squared_height():
+    """The preimage solver's Jacobian in (x, y, s = zh^2) equals the key-point matrix
+    diag(-1, -1, 1) T_s (Eq. eq_duvw_relp) with its z column divided by 2 zh."""
+    for p in PROBES:
+        Jt = oracle.jacobian_ts(RECT, ZBAR, KMIN, KMAX, p)
+        zh = p[2] - ZBAR
+        Js = oracle.jacobian_s(RECT, KMIN, KMAX, p[0], p[1], zh * zh)
+        np.testing.assert_allclose(Js[:, :2], Jt[:, :2], rtol=1e-10, atol=1e-8)
+        np.testing.assert_allclose(Js[:, 2], Jt[:, 2] / (2 * zh), rtol=1e-10, atol=1e-8)
+
+
 # --------------------------------------------------------------------------- preimage
 def test_preimage_round_trip():
     rng = np.random.default_rng(11)

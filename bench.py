@@ -183,7 +183,10 @@ def run_gpu(args):
     wl = args.workload
     s = _scene(wl, rank)
     echo = synth.scene_echo(s, device="cuda")
-    cfg = PLAN_CFG[wl]
+    cfg = dict(PLAN_CFG[wl])
+    for key, val in (("leaf_size", args.leaf), ("taps", args.taps), ("eta", args.eta)):
+        if val is not None:
+            cfg[key] = val
     grid = s.grid
     torch.cuda.synchronize()
 
@@ -433,6 +436,9 @@ def main():
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf", type=int, default=None, help="override the plan's leaf size")
+    ap.add_argument("--taps", type=int, default=None, help="override the interpolation taps")
+    ap.add_argument("--eta", type=float, default=None, help="override the base lattice density")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -202,6 +202,14 @@ int hhffbp_plan_preimages(const hh_plan* plan, int64_t node, const double* targe
  */
 int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, void* cuda_stream);
 
+/*
+ * hh_release_cached_memory -- free the device blocks that destroyed plans left
+ * in the library's cache (plans reuse them instead of calling cudaMalloc; at
+ * most 64 GiB stay cached, and an allocation failure first empties the cache of
+ * that device).  Call when no plan is being created or destroyed.
+ */
+int hh_release_cached_memory(void);
+
 /* Human-readable status text (static string). */
 const char* hh_status_string(int status);
 

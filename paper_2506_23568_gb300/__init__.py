@@ -36,7 +36,8 @@ HH_FLAG_HOST_ONLY = 1
 SYMBOLS = ["hhffbp_default_config", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
            "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
            "hhffbp_plan_stage_times", "hhffbp_plan_preimages",
-           "bpa_form_image", "hhffbp_adjoint", "hh_status_string", "hh_last_cuda_error"]
+           "bpa_form_image", "hhffbp_adjoint", "hh_status_string", "hh_last_cuda_error",
+           "hh_release_cached_memory"]
 STAGE_NAMES = {0: "range_compression", 1: "need_final", 2: "need_level", 3: "leaf_subimages", 4: "merge",
                5: "final", 6: "h2d", 7: "d2h"}
 
@@ -107,6 +108,7 @@ def _declare(L):
     L.hh_status_string.argtypes = [ctypes.c_int]
     L.hh_status_string.restype = ctypes.c_char_p
     L.hh_last_cuda_error.argtypes = []
+    L.hh_release_cached_memory.argtypes = []
     for name in SYMBOLS:
         f = getattr(L, name)
         if name != "hh_status_string":
@@ -280,6 +282,11 @@ class Plan:
     def adjoint(self, image, out=None, stream=None):
         _check(lib().hhffbp_adjoint(self._h, _buffer_ptr(image), _buffer_ptr(image), _stream_ptr(stream)),
                "hhffbp_adjoint")
+
+
+def release_cached_memory():
+    """Free device blocks cached by the library for reuse by later plans."""
+    _check(lib().hh_release_cached_memory(), "release_cached_memory")
 
 
 def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16):

@@ -62,7 +62,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
                    "-I", INCLUDE, "-c", src, "-o", obj, *extra_nvcc]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INCLUDE, "-I",
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-I", INCLUDE, "-I",
                    os.path.join(cuda, "include"), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -78,7 +78,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("library build failed:\n" + msg)
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xcompiler", "-pthread"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     return LIB

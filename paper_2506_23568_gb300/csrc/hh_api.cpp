@@ -1,9 +1,13 @@
 // C ABI of the HHFFBPA library: argument checks, device workspace, launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 
 #include "hh_internal.h"
 
@@ -39,26 +43,95 @@ bool is_host_pointer(const void* ptr) {
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
+// Per-device cache of device blocks released by destroyed plans, so that the
+// per-scan plan of a repeated workload does not pay cudaMalloc/cudaFree.
+// Sizes are rounded up to 2 MiB; a request takes the smallest cached block of
+// at least its size and at most twice it.  hh_release_cached_memory() frees all.
+struct BlockCache {
+    std::mutex mu;
+    std::multimap<std::pair<int, size_t>, void*> free_blocks;  // (device, bytes) -> block
+    std::unordered_map<void*, std::pair<int, size_t>> sizes;   // every live or cached block
+    size_t cached_bytes = 0;
+    static constexpr size_t kCap = (size_t)64 << 30;
+};
+BlockCache& cache() {
+    static BlockCache* c = new BlockCache();  // never destroyed: safe at process exit
+    return *c;
+}
+
+size_t round_block(size_t bytes) {
+    const size_t g = (size_t)2 << 20;
+    return bytes <= ((size_t)1 << 20) ? ((bytes + 255) & ~(size_t)255) : (bytes + g - 1) / g * g;
+}
+
+cudaError_t cached_malloc(void** ptr, size_t bytes, int device) {
+    BlockCache& c = cache();
+    const size_t want = round_block(bytes);
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.free_blocks.lower_bound({device, want});
+        if (it != c.free_blocks.end() && it->first.first == device && it->first.second <= 2 * want) {
+            *ptr = it->second;
+            c.cached_bytes -= it->first.second;
+            c.free_blocks.erase(it);
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMalloc(ptr, want);
+    if (e == cudaErrorMemoryAllocation) {  // return this device's cached blocks and retry once
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(c.mu);
+        for (auto it = c.free_blocks.begin(); it != c.free_blocks.end();) {
+            if (it->first.first == device) {
+                cudaFree(it->second);
+                c.sizes.erase(it->second);
+                c.cached_bytes -= it->first.second;
+                it = c.free_blocks.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        e = cudaMalloc(ptr, want);
+    }
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(c.mu);
+        c.sizes[*ptr] = {device, want};
+    }
+    return e;
+}
+
+void cached_free(void* ptr) {
+    BlockCache& c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.sizes.find(ptr);
+    if (it == c.sizes.end()) {
+        cudaFree(ptr);
+        return;
+    }
+    if (c.cached_bytes + it->second.second > BlockCache::kCap) {
+        cudaFree(ptr);
+        c.sizes.erase(it);
+        return;
+    }
+    c.free_blocks.insert({it->second, ptr});
+    c.cached_bytes += it->second.second;
+}
+
 int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    HH_CUDA(cudaMalloc(ptr, bytes));
+    HH_CUDA(cached_malloc(ptr, bytes, p->device));
     p->workspace_bytes += (int64_t)bytes;
     return HH_OK;
 }
 
 void free_device(hh_plan* p) {
-    void** bufs[] = {&p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
+    void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz};
+                     &p->d_need, &p->d_xyz, &p->d_fb, &p->d_fb_val, &p->d_fb_count};
     for (void** b : bufs)
         if (*b) {
-            cudaFree(*b);
+            cached_free(*b);
             *b = nullptr;
-        }
-    for (void*& t : p->d_tiles)
-        if (t) {
-            cudaFree(t);
-            t = nullptr;
         }
     for (void*& ev : p->events)
         if (ev) {
@@ -190,15 +263,25 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     std::vector<float> tw = hh::twiddle_table(p->n_fft);
     const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
     HH_TRY(dev_alloc(p, &p->d_nodes, sizeof(hh::DNode) * dn.size()));
-    p->d_tiles.assign(p->n_levels, nullptr);
-    for (int l = 0; l < p->n_levels; ++l)
-        HH_TRY(dev_alloc(p, &p->d_tiles[l], sizeof(hh::DTile) * p->tiles[l].size()));
+    HH_TRY(dev_alloc(p, &p->d_tile_off, sizeof(int64_t) * p->tile_off.size()));
     HH_TRY(dev_alloc(p, &p->d_mem_pos, sizeof(double) * mem_pos.size()));
     HH_TRY(dev_alloc(p, &p->d_perm, sizeof(int64_t) * n_pos));
     HH_TRY(dev_alloc(p, &p->d_prof, 8 * (size_t)n_pos * (size_t)p->gate_n));
     if (p->max_pool > 0) {
         HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
         HH_TRY(dev_alloc(p, &p->d_pool[1], 8 * (size_t)p->max_pool));
+    }
+    if (p->n_levels > 1) {
+        // deferred-fallback queue: one level at a time
+        int64_t widest = 0;
+        for (int l = 1; l < p->n_levels; ++l) {
+            const int64_t nch = p->nodes[p->level_start[l]].nchild;
+            widest = std::max(widest, p->level_samples[l] * nch);
+        }
+        p->fb_cap = std::min<int64_t>(std::max<int64_t>(widest / 4, 1 << 16), (int64_t)1 << 25);
+        HH_TRY(dev_alloc(p, &p->d_fb, sizeof(hh::FbRecord) * (size_t)p->fb_cap));
+        HH_TRY(dev_alloc(p, &p->d_fb_val, 8 * (size_t)p->fb_cap));
+        HH_TRY(dev_alloc(p, &p->d_fb_count, 16));
     }
     if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, (size_t)p->need_total));
     if (p->xyz_total > 0) HH_TRY(dev_alloc(p, &p->d_xyz, 16 * (size_t)p->xyz_total));
@@ -208,9 +291,8 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     HH_TRY(dev_alloc(p, &p->d_echo_stage, 8 * (size_t)n_pos * (size_t)n_f));
     HH_TRY(dev_alloc(p, &p->d_image_stage, 8 * (size_t)n_vox));
     HH_TRY(upload(p->d_nodes, dn.data(), sizeof(hh::DNode) * dn.size(), s));
-    for (int l = 0; l < p->n_levels; ++l)
-        if (!p->tiles[l].empty())
-            HH_TRY(upload(p->d_tiles[l], p->tiles[l].data(), sizeof(hh::DTile) * p->tiles[l].size(), s));
+    if (!p->tile_off.empty())
+        HH_TRY(upload(p->d_tile_off, p->tile_off.data(), sizeof(int64_t) * p->tile_off.size(), s));
     HH_TRY(upload(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), s));
     HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
     HH_TRY(upload(p->d_twiddle, tw.data(), sizeof(float) * tw.size(), s));
@@ -323,11 +405,15 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
         HH_LAUNCH(hh::launch_stage0(p, kc, cuda_stream));
         for (int l = 1; l + 1 < p->n_levels; ++l) {
             HH_MARK(HH_STAGE_MERGE, l);
+            HH_CUDA(cudaMemsetAsync(p->d_fb_count, 0, 8, s));
             HH_LAUNCH(hh::launch_merge(p, kc, l, cuda_stream));
+            HH_LAUNCH(hh::launch_fallbacks(p, kc, l, p->d_pool[l & 1], cuda_stream));
         }
     }
     HH_MARK(HH_STAGE_FINAL, p->n_levels - 1);
+    if (p->n_levels > 1) HH_CUDA(cudaMemsetAsync(p->d_fb_count, 0, 8, s));
     HH_LAUNCH(hh::launch_final(p, kc, image, cuda_stream));
+    if (p->n_levels > 1) HH_LAUNCH(hh::launch_fallbacks(p, kc, p->n_levels - 1, image, cuda_stream));
     if (host_img) {
         HH_MARK(HH_STAGE_D2H, -1);
         HH_CUDA(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));
@@ -495,6 +581,22 @@ int hhffbp_plan_preimages(const hh_plan* p, int64_t node, const double* targets,
 int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, void* cuda_stream) {
     (void)plan; (void)image_c64; (void)echo_c64; (void)cuda_stream;
     return HH_ERR_UNIMPLEMENTED;
+}
+
+int hh_release_cached_memory(void) {
+    BlockCache& c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& kv : c.free_blocks) {
+        cudaSetDevice(kv.first.first);
+        cudaFree(kv.second);
+        c.sizes.erase(kv.second);
+    }
+    c.free_blocks.clear();
+    c.cached_bytes = 0;
+    cudaSetDevice(cur);
+    return HH_OK;
 }
 
 const char* hh_status_string(int status) {

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "hh_internal.h"
 
@@ -67,32 +68,47 @@ struct Sub {
     }
 };
 
-// Solve A^T x = rhs for a 3x3 A by Gaussian elimination with partial pivoting.
-bool solve_transposed(const double A[3][3], const double rhs[3], double x[3]) {
-    double M[3][4];
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) M[i][j] = A[j][i];
-        M[i][3] = rhs[i];
-    }
-    for (int c = 0; c < 3; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < 3; ++r)
-            if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
-        if (!(std::fabs(M[piv][c]) > 0)) return false;
-        if (piv != c)
-            for (int j = 0; j < 4; ++j) std::swap(M[c][j], M[piv][j]);
-        for (int r = c + 1; r < 3; ++r) {
-            double f = M[r][c] / M[c][c];
-            for (int j = c; j < 4; ++j) M[r][j] -= f * M[c][j];
+// LU factorisation (partial pivoting) of A^T for a 3x3 A, then solves A^T x = rhs.
+struct LU3 {
+    double M[3][3];
+    int piv[3];
+    bool ok;
+    explicit LU3(const double A[3][3]) : ok(true) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = A[j][i];
+        for (int i = 0; i < 3; ++i) piv[i] = i;
+        for (int c = 0; c < 3; ++c) {
+            int pr = c;
+            for (int r = c + 1; r < 3; ++r)
+                if (std::fabs(M[r][c]) > std::fabs(M[pr][c])) pr = r;
+            if (!(std::fabs(M[pr][c]) > 0)) {
+                ok = false;
+                return;
+            }
+            if (pr != c) {
+                for (int j = 0; j < 3; ++j) std::swap(M[c][j], M[pr][j]);
+                std::swap(piv[c], piv[pr]);
+            }
+            for (int r = c + 1; r < 3; ++r) {
+                M[r][c] /= M[c][c];
+                for (int j = c + 1; j < 3; ++j) M[r][j] -= M[r][c] * M[c][j];
+            }
         }
     }
-    for (int i = 2; i >= 0; --i) {
-        double s = M[i][3];
-        for (int j = i + 1; j < 3; ++j) s -= M[i][j] * x[j];
-        x[i] = s / M[i][i];
+    void solve(const double rhs[3], double x[3]) const {
+        double y[3];
+        for (int i = 0; i < 3; ++i) {
+            double s = rhs[piv[i]];
+            for (int j = 0; j < i; ++j) s -= M[i][j] * y[j];
+            y[i] = s;
+        }
+        for (int i = 2; i >= 0; --i) {
+            double s = y[i];
+            for (int j = i + 1; j < 3; ++j) s -= M[i][j] * x[j];
+            x[i] = s / M[i][i];
+        }
     }
-    return true;
-}
+};
 
 struct GridBox {
     double lo[3], hi[3];
@@ -165,13 +181,15 @@ void spectral_extent(const Sub& s, double zlo, double zhi, const GridBox& B, dou
                                iz == 0 ? B.lo[2] : (iz == 2 ? B.hi[2] : 0.5 * (B.lo[2] + B.hi[2]))};
                 double kcv[3], J[3][3];
                 s.centre_and_jacobian(p, kcv, J);
+                const LU3 lu(J);
+                if (!lu.ok) continue;
                 for (int q = 0; q < 16; ++q)
                     for (double Z : {zlo, zhi})
                         for (double k : {s.kmin, s.kmax}) {
                             double K[3], rhs[3], kap[3];
                             Sub::kvec(px[q], py[q], Z, p, k, K);
                             for (int i = 0; i < 3; ++i) rhs[i] = K[i] - kcv[i];
-                            if (!solve_transposed(J, rhs, kap)) continue;
+                            lu.solve(rhs, kap);
                             for (int i = 0; i < 3; ++i) rho[i] = std::max(rho[i], std::fabs(kap[i]) / kPi);
                         }
             }
@@ -368,24 +386,39 @@ int build_host_plan(hh_plan* p) {
     // capped at 2m for u, v with 4-way merges (their steps halve per level);
     // plus one step.
     const int64_t m = cfg.taps / 2;
+    const int64_t n_lattice_nodes = p->level_start[p->n_levels - 1];
+    auto lattice_of = [&](int64_t k) {
+        HNode& nd = p->nodes[k];
+        Sub s{nd.rect[0], nd.rect[1], nd.rect[2], nd.rect[3], nd.zbar, p->kmin, p->kmax};
+        double mn[3], mx[3], rho[3];
+        uvn_extremes(s, B, mn, mx);
+        spectral_extent(s, nd.zmin, nd.zmax, B, rho);
+        const int64_t pad_n = m * nd.t + 1;
+        const int64_t pad_uv = cfg.merge_factor == 4 ? std::min(m * nd.t, 2 * m) + 1 : pad_n;
+        const int64_t pad[3] = {pad_uv, pad_uv, pad_n};
+        for (int i = 0; i < 3; ++i) {
+            nd.eta[i] = (double)cfg.eta * rho[i];
+            nd.lo[i] = mn[i] - (double)pad[i] / nd.eta[i];
+            nd.N[i] = (int64_t)std::ceil((mx[i] - mn[i]) * nd.eta[i]) + 1 + 2 * pad[i];
+        }
+    };
+    // nodes are independent: spread them over the host threads (same results in any split)
+    {
+        const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+        const int64_t nt = std::min<int64_t>(std::min<int64_t>(hw, 32), std::max<int64_t>(1, n_lattice_nodes / 8));
+        std::vector<std::thread> pool;
+        for (int64_t t = 0; t < nt; ++t)
+            pool.emplace_back([&, t]() {
+                for (int64_t k = t; k < n_lattice_nodes; k += nt) lattice_of(k);
+            });
+        for (auto& th : pool) th.join();
+    }
     p->level_samples.assign(p->n_levels, 0);
     p->max_pool = 0;
     for (int l = 0; l + 1 < p->n_levels; ++l) {
         int64_t off = 0;
         for (int64_t k = p->level_start[l]; k < p->level_start[l + 1]; ++k) {
             HNode& nd = p->nodes[k];
-            Sub s{nd.rect[0], nd.rect[1], nd.rect[2], nd.rect[3], nd.zbar, p->kmin, p->kmax};
-            double mn[3], mx[3], rho[3];
-            uvn_extremes(s, B, mn, mx);
-            spectral_extent(s, nd.zmin, nd.zmax, B, rho);
-            const int64_t pad_n = m * nd.t + 1;
-            const int64_t pad_uv = cfg.merge_factor == 4 ? std::min(m * nd.t, 2 * m) + 1 : pad_n;
-            const int64_t pad[3] = {pad_uv, pad_uv, pad_n};
-            for (int i = 0; i < 3; ++i) {
-                nd.eta[i] = (double)cfg.eta * rho[i];
-                nd.lo[i] = mn[i] - (double)pad[i] / nd.eta[i];
-                nd.N[i] = (int64_t)std::ceil((mx[i] - mn[i]) * nd.eta[i]) + 1 + 2 * pad[i];
-            }
             nd.pool_off = off;
             off += nd.N[0] * nd.N[1] * nd.N[2];
         }
@@ -448,24 +481,26 @@ int build_host_plan(hh_plan* p) {
         p->gate_wrap = true;
     }
 
-    // ---- launch tiles
-    p->tiles.assign(p->n_levels, {});
-    const int TU = kTile0, TV = kTile1, TN = kTile2;
-    for (int l = 0; l + 1 < p->n_levels; ++l)
+    // ---- launch tiles: kTile0 x kTile1 x kTile2 boxes of each node's lattice, and of the grid
+    p->level_tiles.assign(p->n_levels, 0);
+    p->tile_off.clear();
+    p->tile_off_base.assign(p->n_levels, 0);
+    for (int l = 0; l + 1 < p->n_levels; ++l) {
+        p->tile_off_base[l] = (int64_t)p->tile_off.size();
+        int64_t t = 0;
         for (int64_t k = p->level_start[l]; k < p->level_start[l + 1]; ++k) {
             const HNode& nd = p->nodes[k];
-            for (int64_t a = 0; a < nd.N[0]; a += TU)
-                for (int64_t b = 0; b < nd.N[1]; b += TV)
-                    for (int64_t c = 0; c < nd.N[2]; c += TN)
-                        p->tiles[l].push_back(DTile{(int32_t)k, (int32_t)a, (int32_t)b, (int32_t)c});
+            p->tile_off.push_back(t);
+            t += ((nd.N[0] + kTile0 - 1) / kTile0) * ((nd.N[1] + kTile1 - 1) / kTile1) *
+                 ((nd.N[2] + kTile2 - 1) / kTile2);
         }
+        p->tile_off.push_back(t);
+        p->level_tiles[l] = t;
+    }
     {
         const hh_grid& g = p->grid;
-        const int TX = kTile0, TY = kTile1, TZ = kTile2;
-        auto& tl = p->tiles[p->n_levels - 1];
-        for (int c = 0; c < g.nz; c += TZ)
-            for (int b = 0; b < g.ny; b += TY)
-                for (int a = 0; a < g.nx; a += TX) tl.push_back(DTile{-1, a, b, c});
+        p->level_tiles[p->n_levels - 1] = (int64_t)((g.nx + kTile0 - 1) / kTile0) * ((g.ny + kTile1 - 1) / kTile1) *
+                                          ((g.nz + kTile2 - 1) / kTile2);
     }
     p->wtable = weight_table(cfg.taps, cfg.eta);
     return HH_OK;

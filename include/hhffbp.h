@@ -42,6 +42,7 @@ extern "C" {
 #define HH_ERR_DEVICE_FLAG 6      /* a kernel raised an error counter (see hhffbp_plan_counters) */
 #define HH_ERR_UNIMPLEMENTED 7
 #define HH_ERR_HOST_ONLY 8        /* the plan was built with HH_FLAG_HOST_ONLY and holds no device state */
+#define HH_ERR_SCRATCH_LIMIT 9    /* the problem needs more than the fixed workspace of bpa_form_image_noalloc */
 
 /* ---- plan flags --------------------------------------------------------- */
 #define HH_FLAG_HOST_ONLY 1u      /* build tree and sampling grids on the host only (no CUDA calls) */
@@ -183,6 +184,34 @@ int hhffbp_plan_stage_times(const hh_plan* plan, float* ms, int32_t* kind, int32
  */
 int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
                    const hh_config* cfg, const void* echo_c64, void* image_c64, void* cuda_stream);
+
+/*
+ * bpa_form_image_noalloc -- bpa_form_image for callers that cannot allocate
+ * memory during the call.  The paper has no counterpart: it is an interface
+ * variant of the same computation (Eqs. eq2_rangecompression and
+ * eq2_bpatimedomain), with the same arguments and results as bpa_form_image.
+ *
+ * Workspace: a fixed device array of HH_NOALLOC_SCRATCH_BYTES per device,
+ * reserved when the library's module is loaded; the call makes no device or
+ * host allocation.  It holds the counters, the twiddle table (16 n_fft bytes),
+ * the trajectory (24 n_pos bytes) and the range profiles (8 n_pos gate_n bytes,
+ * gate_n = range bins spanned by all voxel-position distances, <= n_fft), each
+ * rounded up to 256 bytes.  Larger problems return HH_ERR_SCRATCH_LIMIT before
+ * any device work.  The first call on a device looks the workspace up (and may
+ * load the module); make it before recording a stream.
+ *
+ * echo_c64 and image_c64 must be device (or managed) memory of the current
+ * device (no host staging, which would need a buffer); traj_xyz and freqs_hz
+ * are host arrays, copied to the workspace on cuda_stream.  Asynchronous on
+ * cuda_stream.  Calls that overlap in time on the same device (any streams or
+ * host threads) share the workspace and race: serialise them.
+ * Errors: HH_ERR_ARG (also for host or foreign-device echo/image),
+ * HH_ERR_FREQ_NONUNIFORM, HH_ERR_SCRATCH_LIMIT, HH_ERR_CUDA.
+ */
+#define HH_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int bpa_form_image_noalloc(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f,
+                           const hh_grid* grid, const hh_config* cfg, const void* echo_c64, void* image_c64,
+                           void* cuda_stream);
 
 /*
  * hhffbp_plan_preimages -- diagnostic: run the device preimage solver of the

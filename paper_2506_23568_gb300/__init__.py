@@ -19,7 +19,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Grid", "Config", "Plan", "bpa_form_image", "lib", "LibraryError", "status_string", "SYMBOLS"]
+__all__ = ["Grid", "Config", "Plan", "bpa_form_image", "bpa_form_image_noalloc", "lib", "LibraryError", "status_string", "SYMBOLS"]
 
 HH_OK = 0
 HH_ERR_ARG = 1
@@ -30,13 +30,14 @@ HH_ERR_PLAN_NONCONVERGED = 5
 HH_ERR_DEVICE_FLAG = 6
 HH_ERR_UNIMPLEMENTED = 7
 HH_ERR_HOST_ONLY = 8
+HH_ERR_SCRATCH_LIMIT = 9
 HH_FLAG_HOST_ONLY = 1
 
 # every symbol declared in include/hhffbp.h
 SYMBOLS = ["hhffbp_default_config", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
            "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
            "hhffbp_plan_stage_times", "hhffbp_plan_preimages",
-           "bpa_form_image", "hhffbp_adjoint", "hh_status_string", "hh_last_cuda_error",
+           "bpa_form_image", "bpa_form_image_noalloc", "hhffbp_adjoint", "hh_status_string", "hh_last_cuda_error",
            "hh_release_cached_memory"]
 STAGE_NAMES = {0: "range_compression", 1: "need_final", 2: "need_level", 3: "leaf_subimages", 4: "merge",
                5: "final", 6: "h2d", 7: "d2h"}
@@ -303,4 +304,18 @@ def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16):
                                 f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
                                 ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
            "bpa_form_image")
+    return out
+
+
+def bpa_form_image_noalloc(traj, freqs, grid, echo, out, stream=None, range_os=16):
+    """Direct BPA through the entry point with a fixed device workspace (no
+    allocation inside the call).  echo and out must be device tensors of the
+    current device; out is complex64 [nz][ny][nx] and is required."""
+    t, f = _f64(traj), _f64(freqs)
+    g = Grid.from_any(grid)
+    cfg = Config(range_os=range_os)
+    _check(lib().bpa_form_image_noalloc(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
+                                        f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
+                                        ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
+           "bpa_form_image_noalloc")
     return out

@@ -212,6 +212,10 @@ int upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 
 }  // namespace
 
+namespace hh {
+int note_cuda_error(int cuda_error) { return fail_cuda((cudaError_t)cuda_error); }
+}  // namespace hh
+
 extern "C" {
 
 int hhffbp_default_config(hh_config* cfg) {
@@ -610,6 +614,7 @@ const char* hh_status_string(int status) {
         case HH_ERR_DEVICE_FLAG: return "a kernel raised an error counter";
         case HH_ERR_UNIMPLEMENTED: return "not implemented";
         case HH_ERR_HOST_ONLY: return "plan has no device state (built host-only)";
+        case HH_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed workspace of bpa_form_image_noalloc";
         default: return "unknown status";
     }
 }

@@ -179,4 +179,7 @@ int launch_preimage_probe(const hh_plan* p, const KConst& kc, int node, const do
                           void* stream);
 KConst make_kconst(const hh_plan* p);
 
+// hh_api.cpp: record a CUDA error for hh_last_cuda_error() and map it to a status
+int note_cuda_error(int cuda_error);
+
 }  // namespace hh

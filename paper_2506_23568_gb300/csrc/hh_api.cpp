@@ -127,7 +127,7 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz, &p->d_fb, &p->d_fb_val, &p->d_fb_count};
+                     &p->d_need, &p->d_xyz};
     for (void** b : bufs)
         if (*b) {
             cached_free(*b);
@@ -275,18 +275,6 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
         HH_TRY(dev_alloc(p, &p->d_pool[1], 8 * (size_t)p->max_pool));
     }
-    if (p->n_levels > 1) {
-        // deferred-fallback queue: one level at a time
-        int64_t widest = 0;
-        for (int l = 1; l < p->n_levels; ++l) {
-            const int64_t nch = p->nodes[p->level_start[l]].nchild;
-            widest = std::max(widest, p->level_samples[l] * nch);
-        }
-        p->fb_cap = std::min<int64_t>(std::max<int64_t>(widest / 4, 1 << 16), (int64_t)1 << 25);
-        HH_TRY(dev_alloc(p, &p->d_fb, sizeof(hh::FbRecord) * (size_t)p->fb_cap));
-        HH_TRY(dev_alloc(p, &p->d_fb_val, 8 * (size_t)p->fb_cap));
-        HH_TRY(dev_alloc(p, &p->d_fb_count, 16));
-    }
     if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, (size_t)p->need_total));
     if (p->xyz_total > 0) HH_TRY(dev_alloc(p, &p->d_xyz, 16 * (size_t)p->xyz_total));
     HH_TRY(dev_alloc(p, &p->d_twiddle, sizeof(float) * tw.size()));
@@ -409,15 +397,11 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
         HH_LAUNCH(hh::launch_stage0(p, kc, cuda_stream));
         for (int l = 1; l + 1 < p->n_levels; ++l) {
             HH_MARK(HH_STAGE_MERGE, l);
-            HH_CUDA(cudaMemsetAsync(p->d_fb_count, 0, 8, s));
             HH_LAUNCH(hh::launch_merge(p, kc, l, cuda_stream));
-            HH_LAUNCH(hh::launch_fallbacks(p, kc, l, p->d_pool[l & 1], cuda_stream));
         }
     }
     HH_MARK(HH_STAGE_FINAL, p->n_levels - 1);
-    if (p->n_levels > 1) HH_CUDA(cudaMemsetAsync(p->d_fb_count, 0, 8, s));
     HH_LAUNCH(hh::launch_final(p, kc, image, cuda_stream));
-    if (p->n_levels > 1) HH_LAUNCH(hh::launch_fallbacks(p, kc, p->n_levels - 1, image, cuda_stream));
     if (host_img) {
         HH_MARK(HH_STAGE_D2H, -1);
         HH_CUDA(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));

@@ -83,20 +83,9 @@ struct KConst {
 };
 
 // Device counters (int64): see hhffbp_plan_counters.
-// CNT_NEEDED + level: samples evaluated at that level (the root: voxels);
-// CNT_FB_LEVEL + level: exact fallbacks queued at that level.
+// CNT_NEEDED + level: samples evaluated at that level (the root: voxels).
 enum Counter { CNT_FALLBACK = 0, CNT_INFEASIBLE = 1, CNT_NEWTON_FAIL = 2, CNT_GATE_MISS = 3, CNT_ERROR = 4,
-               CNT_FALLBACK_UPDATES = 5, CNT_FB_OVERFLOW = 6, CNT_NEEDED = 8, CNT_FB_LEVEL = 8 + kMaxLevels,
-               CNT_N = 8 + 2 * kMaxLevels };
-
-// Deferred exact fallback: the contribution of child `child` at one output sample,
-// exp(j theta) * g_child(p), p in the child's frame; summed later by a warp per record.
-struct FbRecord {
-    int64_t out;   // output index (level pool or image)
-    int32_t child; // node index
-    float x, y, z; // point in the child's frame
-    float c, s;    // exp(j theta)
-};
+               CNT_FALLBACK_UPDATES = 5, CNT_NEEDED = 8, CNT_N = 8 + 2 * kMaxLevels };
 
 }  // namespace hh
 
@@ -134,10 +123,6 @@ struct hh_plan {
     void* d_twiddle = nullptr;   // float2[2 n_fft]
     void* d_wtable = nullptr;
     void* d_counters = nullptr;  // int64[CNT_N]
-    void* d_fb = nullptr;        // FbRecord[fb_cap] deferred fallbacks of one level
-    void* d_fb_val = nullptr;    // float2[fb_cap] their contributions
-    void* d_fb_count = nullptr;  // unsigned long long: records queued at the current level
-    int64_t fb_cap = 0;
     void* d_need = nullptr;      // uint8 per lattice sample of every non-root level (need_base offsets)
     void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
     std::vector<int64_t> need_base;  // per level: first sample in d_need
@@ -174,7 +159,6 @@ int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* strea
 int launch_stage0(const hh_plan* p, const KConst& kc, void* stream);
 int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_final(const hh_plan* p, const KConst& kc, void* d_image, void* stream);
-int launch_fallbacks(const hh_plan* p, const KConst& kc, int level, void* out, void* stream);
 int launch_preimage_probe(const hh_plan* p, const KConst& kc, int node, const double* d_tgt, int64_t n, double* d_out,
                           void* stream);
 KConst make_kconst(const hh_plan* p);

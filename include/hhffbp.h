@@ -194,7 +194,7 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
  * Workspace: a fixed device array of HH_NOALLOC_SCRATCH_BYTES per device,
  * reserved when the library's module is loaded; the call makes no device or
  * host allocation.  It holds the counters, the twiddle table (16 n_fft bytes),
- * the trajectory (24 n_pos bytes) and the range profiles (8 n_pos gate_n bytes,
+ * the trajectory (24 n_pos bytes) and the range profiles (16 n_pos gate_n bytes,
  * gate_n = range bins spanned by all voxel-position distances, <= n_fft), each
  * rounded up to 256 bytes.  Larger problems return HH_ERR_SCRATCH_LIMIT before
  * any device work.  The first call on a device looks the workspace up (and may

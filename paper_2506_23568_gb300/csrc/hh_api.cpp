@@ -270,7 +270,7 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     HH_TRY(dev_alloc(p, &p->d_tile_off, sizeof(int64_t) * p->tile_off.size()));
     HH_TRY(dev_alloc(p, &p->d_mem_pos, sizeof(double) * mem_pos.size()));
     HH_TRY(dev_alloc(p, &p->d_perm, sizeof(int64_t) * n_pos));
-    HH_TRY(dev_alloc(p, &p->d_prof, 8 * (size_t)n_pos * (size_t)p->gate_n));
+    HH_TRY(dev_alloc(p, &p->d_prof, 16 * (size_t)n_pos * (size_t)p->gate_n));
     if (p->max_pool > 0) {
         HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
         HH_TRY(dev_alloc(p, &p->d_pool[1], 8 * (size_t)p->max_pool));
@@ -520,7 +520,7 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
         }                                      \
     } while (0)
     HH_STEP(cudaMallocAsync(&d_traj, sizeof(double) * 3 * n_pos, s));
-    HH_STEP(cudaMallocAsync(&d_prof, 8 * (size_t)n_pos * (size_t)tmp.gate_n, s));
+    HH_STEP(cudaMallocAsync(&d_prof, 16 * (size_t)n_pos * (size_t)tmp.gate_n, s));
     HH_STEP(cudaMallocAsync(&d_tw, sizeof(float) * tw.size(), s));
     HH_STEP(cudaMallocAsync(&d_cnt, sizeof(int64_t) * hh::CNT_N, s));
     const void* echo = echo_c64;

@@ -115,7 +115,7 @@ extern "C" int bpa_form_image_noalloc(const double* traj_xyz, int64_t n_pos, con
     const size_t off_tw = align256(sizeof(int64_t) * hh::CNT_N);
     const size_t off_traj = off_tw + align256(sizeof(float2) * 2 * (size_t)tmp.n_fft);
     const size_t off_prof = off_traj + align256(sizeof(double) * 3 * (size_t)n_pos);
-    const size_t need = off_prof + sizeof(float2) * (size_t)n_pos * (size_t)tmp.gate_n;
+    const size_t need = off_prof + sizeof(float4) * (size_t)n_pos * (size_t)tmp.gate_n;
     if (need > (size_t)HH_NOALLOC_SCRATCH_BYTES) return HH_ERR_SCRATCH_LIMIT;
 
     void* base = nullptr;

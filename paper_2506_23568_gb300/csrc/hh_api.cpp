@@ -127,7 +127,7 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz};
+                     &p->d_need, &p->d_xyz, &p->d_leafv};
     for (void** b : bufs)
         if (*b) {
             cached_free(*b);
@@ -264,12 +264,26 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     std::vector<double> mem_pos(3 * (size_t)n_pos);
     for (int64_t q = 0; q < n_pos; ++q)
         for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
+    // leaf members relative to their leaf's centre: v = centre - p' and |v|^2 / 2 (FP32)
+    std::vector<float> leafv(4 * (size_t)n_pos, 0.f);
+    for (int64_t j = p->level_start[0]; j < p->level_start[1]; ++j) {
+        const hh::DNode& L = dn[j];
+        for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
+            const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
+                        vz = (float)(L.cz - mem_pos[3 * q + 2]);
+            leafv[4 * q] = vx;
+            leafv[4 * q + 1] = vy;
+            leafv[4 * q + 2] = vz;
+            leafv[4 * q + 3] = 0.5f * std::fmaf(vx, vx, std::fmaf(vy, vy, vz * vz));
+        }
+    }
     std::vector<float> tw = hh::twiddle_table(p->n_fft);
     const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
     HH_TRY(dev_alloc(p, &p->d_nodes, sizeof(hh::DNode) * dn.size()));
     HH_TRY(dev_alloc(p, &p->d_tile_off, sizeof(int64_t) * p->tile_off.size()));
     HH_TRY(dev_alloc(p, &p->d_mem_pos, sizeof(double) * mem_pos.size()));
     HH_TRY(dev_alloc(p, &p->d_perm, sizeof(int64_t) * n_pos));
+    HH_TRY(dev_alloc(p, &p->d_leafv, sizeof(float) * leafv.size()));
     HH_TRY(dev_alloc(p, &p->d_prof, 16 * (size_t)n_pos * (size_t)p->gate_n));
     if (p->max_pool > 0) {
         HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
@@ -287,6 +301,7 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         HH_TRY(upload(p->d_tile_off, p->tile_off.data(), sizeof(int64_t) * p->tile_off.size(), s));
     HH_TRY(upload(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), s));
     HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
+    HH_TRY(upload(p->d_leafv, leafv.data(), sizeof(float) * leafv.size(), s));
     HH_TRY(upload(p->d_twiddle, tw.data(), sizeof(float) * tw.size(), s));
     HH_TRY(upload(p->d_wtable, p->wtable.data(), sizeof(float) * p->wtable.size(), s));
     cudaError_t e = cudaStreamSynchronize(s);

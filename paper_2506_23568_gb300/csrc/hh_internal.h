@@ -118,6 +118,7 @@ struct hh_plan {
     void* d_tile_off = nullptr;  // int64 copy of tile_off
     void* d_mem_pos = nullptr;   // double[n_pos][3], tree order
     void* d_perm = nullptr;      // int64[n_pos]
+    void* d_leafv = nullptr;     // float4[n_pos], tree order: leaf centre - p', |.|^2 / 2 (FP32)
     void* d_prof = nullptr;      // float4[n_pos][gate_n] (P[m], P[m+1] - P[m]), tree order
     void* d_pool[2] = {nullptr, nullptr};
     void* d_twiddle = nullptr;   // float2[2 n_fft]

@@ -41,6 +41,15 @@ WORKLOADS = {
 PLAN_CFG = {"large": dict(leaf_size=256, eta=1.75), "mid": dict(leaf_size=256, eta=1.75),
             "tiny": dict(leaf_size=32)}
 
+# DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
+# benchmark command on the large workload (profiles/launches_large_bench.md); valid for the
+# kernels and plan they were taken with, reported as null otherwise.
+TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.75, 6): 1305.3e6,
+           ("large", "merge", 1, 256, 1.75, 6): 1878.1e6,
+           ("large", "merge", 2, 256, 1.75, 6): 1325.6e6,
+           ("large", "merge", 3, 256, 1.75, 6): 1255.6e6,
+           ("large", "final", 4, 256, 1.75, 6): 2410.9e6}
+
 # Algorithmic work per unit ("Measurement"):
 BPA_FLOP, BPA_MUFU = 25.0, 3.0            # per (voxel, position) update
 MUFU_PER_SM_CLK = 16.0                    # SFU results per SM per clock (sm_100-class)
@@ -295,11 +304,10 @@ def run_gpu(args):
             e2e.append(time.perf_counter() - t0)
         p2.close()
 
-    # kernels of one step: range compression, need passes (final + L-2 levels), leaf subimages,
-    # per merge level (merge, fallbacks, fallback fixup), final level + its fallbacks; then the
-    # direct BPA (range compression + backprojection)
+    # kernels of one step: range compression, demand passes (root + L-2 levels), leaf
+    # subimages, L-2 merges, final merge; then the direct BPA (range compression + backprojection)
     L = info["n_levels"]
-    n_launch = (6 + 4 * (L - 2) if L > 1 else 2) + 2
+    n_launch = (4 + 2 * (L - 2) if L > 1 else 2) + 2
     nr_db = 20 * math.log10(statistics.mean(errs))
     value = total_ms / 1e3 / args.steps  # whole step per volume (reported for the driver clock)
     hh_s = mean_hh / 1e3 / ws
@@ -325,7 +333,9 @@ def run_gpu(args):
         "nrmse_db": nr_db,
         "stages_ms": [[w["stage"], w["level"], round(w["ms"], 3), round(w["roof_ms"], 3), w["bound"]] for w in work],
         "roofline": {"kernel": f'{dom["stage"]}(level {dom["level"]})', "bound": d_bound, "achieved": d_ach,
-                     "peak": d_peak, "unit": d_unit, "frac": d_frac, "traffic": None,
+                     "peak": d_peak, "unit": d_unit, "frac": d_frac,
+                     "traffic": TRAFFIC.get((wl, dom["stage"], dom["level"], cfg.get("leaf_size"),
+                                             plan.config.eta, plan.config.taps)),
                      "peak_source": f'{peaks["source"]} ({MUFU_PER_SM_CLK:g} SFU/clk/SM, {FP32_PER_SM_CLK:g} '
                                     f'FLOP/clk/SM x 152 SMs at the sampled {clk_mhz:.0f} MHz)'},
         "roofline_pipeline": {"roofline_ms": roof_ms, "kernels_ms": hh_kernel_ms,

@@ -304,10 +304,10 @@ def run_gpu(args):
             e2e.append(time.perf_counter() - t0)
         p2.close()
 
-    # kernels of one step: range compression, demand passes (root + L-2 levels), leaf
+    # kernels of one step: range compression, tile warm starts (L-1 levels), demand passes (root + L-2 levels), leaf
     # subimages, L-2 merges, final merge; then the direct BPA (range compression + backprojection)
     L = info["n_levels"]
-    n_launch = (4 + 2 * (L - 2) if L > 1 else 2) + 2
+    n_launch = (4 + 2 * (L - 2) + (L - 1) if L > 1 else 2) + 2
     nr_db = 20 * math.log10(statistics.mean(errs))
     value = total_ms / 1e3 / args.steps  # whole step per volume (reported for the driver clock)
     hh_s = mean_hh / 1e3 / ws

@@ -127,7 +127,7 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz, &p->d_leafv};
+                     &p->d_need, &p->d_xyz, &p->d_leafv, &p->d_tile_ref};
     for (void** b : bufs)
         if (*b) {
             cached_free(*b);
@@ -289,6 +289,15 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
         HH_TRY(dev_alloc(p, &p->d_pool[1], 8 * (size_t)p->max_pool));
     }
+    if (p->n_levels > 1) {  // tile warm starts of the lattice levels
+        p->tile_ref_base.assign(p->n_levels, 0);
+        int64_t tiles = 0;
+        for (int l = 0; l + 1 < p->n_levels; ++l) {
+            p->tile_ref_base[l] = tiles;
+            tiles += p->level_tiles[l];
+        }
+        if (tiles > 0) HH_TRY(dev_alloc(p, &p->d_tile_ref, sizeof(float) * 16 * (size_t)tiles));
+    }
     if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, (size_t)p->need_total));
     if (p->xyz_total > 0) HH_TRY(dev_alloc(p, &p->d_xyz, 16 * (size_t)p->xyz_total));
     HH_TRY(dev_alloc(p, &p->d_twiddle, sizeof(float) * tw.size()));
@@ -401,6 +410,7 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
     if (p->n_levels > 1) {
         // top-down: which lattice samples the image needs (the footprints of needed points)
         HH_MARK(HH_STAGE_NEED_FINAL, p->n_levels - 1);
+        for (int l = 0; l + 1 < p->n_levels; ++l) HH_LAUNCH(hh::launch_tile_refs(p, kc, l, cuda_stream));
         HH_CUDA(cudaMemsetAsync(p->d_need, 0, (size_t)p->need_total, s));
         HH_LAUNCH(hh::launch_need_final(p, kc, cuda_stream));
         for (int l = p->n_levels - 2; l >= 1; --l) {

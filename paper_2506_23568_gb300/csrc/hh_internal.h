@@ -126,6 +126,8 @@ struct hh_plan {
     void* d_counters = nullptr;  // int64[CNT_N]
     void* d_need = nullptr;      // uint8 per lattice sample of every non-root level (need_base offsets)
     void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
+    void* d_tile_ref = nullptr;      // float[16] warm start per launch tile of levels 0..L-2
+    std::vector<int64_t> tile_ref_base;  // per level: first tile in d_tile_ref
     std::vector<int64_t> need_base;  // per level: first sample in d_need
     std::vector<int64_t> xyz_base;   // per level: first sample in d_xyz (levels >= 1)
     int64_t need_total = 0, xyz_total = 0;
@@ -157,6 +159,7 @@ int launch_bpa(const double* d_traj, int64_t n_pos, const void* d_prof, const KC
                void* d_image, void* d_counters, void* stream);
 int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);
 int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* stream);
+int launch_tile_refs(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_stage0(const hh_plan* p, const KConst& kc, void* stream);
 int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_final(const hh_plan* p, const KConst& kc, void* d_image, void* stream);

@@ -127,7 +127,7 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz, &p->d_leafv, &p->d_tile_ref};
+                     &p->d_need, &p->d_xyz, &p->d_leafv, &p->d_tile_ref, &p->d_prof2};
     for (void** b : bufs)
         if (*b) {
             cached_free(*b);
@@ -285,6 +285,7 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     HH_TRY(dev_alloc(p, &p->d_perm, sizeof(int64_t) * n_pos));
     HH_TRY(dev_alloc(p, &p->d_leafv, sizeof(float) * leafv.size()));
     HH_TRY(dev_alloc(p, &p->d_prof, 16 * (size_t)n_pos * (size_t)p->gate_n));
+    HH_TRY(dev_alloc(p, &p->d_prof2, 8 * (size_t)n_pos * (size_t)((p->gate_n + 2) & ~(int64_t)1)));
     if (p->max_pool > 0) {
         HH_TRY(dev_alloc(p, &p->d_pool[0], 8 * (size_t)p->max_pool));
         HH_TRY(dev_alloc(p, &p->d_pool[1], 8 * (size_t)p->max_pool));
@@ -406,7 +407,7 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
     HH_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int64_t) * hh::CNT_N, s));
     const hh::KConst kc = hh::make_kconst(p);
     HH_LAUNCH(hh::launch_rc(echo, static_cast<const int64_t*>(p->d_perm), p->n_pos, p->n_f, p->n_fft, p->gate0,
-                            p->gate_n, p->d_twiddle, p->d_prof, cuda_stream));
+                            p->gate_n, p->d_twiddle, p->d_prof, p->d_prof2, cuda_stream));
     if (p->n_levels > 1) {
         // top-down: which lattice samples the image needs (the footprints of needed points)
         HH_MARK(HH_STAGE_NEED_FINAL, p->n_levels - 1);
@@ -562,7 +563,8 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
     HH_STEP(cudaMemcpyAsync(d_traj, traj_xyz, sizeof(double) * 3 * n_pos, cudaMemcpyHostToDevice, s));
     HH_STEP(cudaMemcpyAsync(d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice, s));
     HH_STEP(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * hh::CNT_N, s));
-    HH_STEP(hh::launch_rc(echo, nullptr, n_pos, n_f, tmp.n_fft, tmp.gate0, tmp.gate_n, d_tw, d_prof, cuda_stream));
+    HH_STEP(hh::launch_rc(echo, nullptr, n_pos, n_f, tmp.n_fft, tmp.gate0, tmp.gate_n, d_tw, d_prof, nullptr,
+                          cuda_stream));
     HH_STEP(hh::launch_bpa(static_cast<const double*>(d_traj), n_pos, d_prof, kc, *grid, image, d_cnt, cuda_stream));
     if (host_img) HH_STEP(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));
     release();

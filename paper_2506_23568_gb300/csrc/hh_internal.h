@@ -120,6 +120,7 @@ struct hh_plan {
     void* d_perm = nullptr;      // int64[n_pos]
     void* d_leafv = nullptr;     // float4[n_pos], tree order: leaf centre - p', |.|^2 / 2 (FP32)
     void* d_prof = nullptr;      // float4[n_pos][gate_n] (P[m], P[m+1] - P[m]), tree order
+    void* d_prof2 = nullptr;     // float2[n_pos][(gate_n + 2) & ~1] P[m] alone (stage-0 windows)
     void* d_pool[2] = {nullptr, nullptr};
     void* d_twiddle = nullptr;   // float2[2 n_fft]
     void* d_wtable = nullptr;
@@ -154,7 +155,7 @@ std::vector<float> weight_table(int taps, double eta);
 
 // hh_kernels.cu (launch wrappers; return cudaError_t as int)
 int launch_rc(const void* echo, const int64_t* d_perm, int64_t n_pos, int n_f, int n_fft, int64_t gate0,
-              int64_t gate_n, const void* d_twiddle, void* d_prof, void* stream);
+              int64_t gate_n, const void* d_twiddle, void* d_prof, void* d_prof2, void* stream);
 int launch_bpa(const double* d_traj, int64_t n_pos, const void* d_prof, const KConst& kc, const hh_grid& g,
                void* d_image, void* d_counters, void* stream);
 int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);

@@ -143,7 +143,7 @@ extern "C" int bpa_form_image_noalloc(const double* traj_xyz, int64_t n_pos, con
     e = cudaGetLastError();
     if (e != cudaSuccess) return hh::note_cuda_error((int)e);
     e = (cudaError_t)hh::launch_rc(echo_c64, nullptr, n_pos, n_f, tmp.n_fft, tmp.gate0, tmp.gate_n, d_tw, d_prof,
-                                   cuda_stream);
+                                   nullptr, cuda_stream);
     if (e != cudaSuccess) return hh::note_cuda_error((int)e);
     e = (cudaError_t)hh::launch_bpa(d_traj, n_pos, d_prof, kc, *grid, image_c64, d_cnt, cuda_stream);
     if (e != cudaSuccess) return hh::note_cuda_error((int)e);

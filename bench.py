@@ -44,11 +44,7 @@ PLAN_CFG = {"large": dict(leaf_size=256, eta=1.75), "mid": dict(leaf_size=256, e
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
 # benchmark command on the large workload (profiles/launches_large_bench.md); valid for the
 # kernels and plan they were taken with, reported as null otherwise.
-TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.75, 6): 1305.3e6,
-           ("large", "merge", 1, 256, 1.75, 6): 1878.1e6,
-           ("large", "merge", 2, 256, 1.75, 6): 1325.6e6,
-           ("large", "merge", 3, 256, 1.75, 6): 1255.6e6,
-           ("large", "final", 4, 256, 1.75, 6): 2410.9e6}
+TRAFFIC = {}
 
 # Algorithmic work per unit ("Measurement"):
 BPA_FLOP, BPA_MUFU = 25.0, 3.0            # per (voxel, position) update
@@ -304,10 +300,11 @@ def run_gpu(args):
             e2e.append(time.perf_counter() - t0)
         p2.close()
 
-    # kernels of one step: range compression, tile warm starts (L-1 levels), demand passes (root + L-2 levels), leaf
-    # subimages, L-2 merges, final merge; then the direct BPA (range compression + backprojection)
+    # kernels of one step: range compression, tile warm starts (L-1 levels), demand passes (root + L-2
+    # levels), leaf subimages, per merge level and the final level: merge, deferred fallbacks, their
+    # fixes; then the direct BPA (range compression + backprojection)
     L = info["n_levels"]
-    n_launch = (4 + 2 * (L - 2) + (L - 1) if L > 1 else 2) + 2
+    n_launch = (5 * L - 3 if L > 1 else 2) + 2
     nr_db = 20 * math.log10(statistics.mean(errs))
     value = total_ms / 1e3 / args.steps  # whole step per volume (reported for the driver clock)
     hh_s = mean_hh / 1e3 / ws

@@ -127,7 +127,8 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz, &p->d_leafv, &p->d_tile_ref, &p->d_prof2};
+                     &p->d_need, &p->d_xyz, &p->d_nodev, &p->d_tile_ref, &p->d_prof2,
+                     &p->d_fb_segs, &p->d_fb_recs, &p->d_fb_vals, &p->d_fb_fixes, &p->d_fb_counts};
     for (void** b : bufs)
         if (*b) {
             cached_free(*b);
@@ -264,17 +265,22 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     std::vector<double> mem_pos(3 * (size_t)n_pos);
     for (int64_t q = 0; q < n_pos; ++q)
         for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
-    // leaf members relative to their leaf's centre: v = centre - p' and |v|^2 / 2 (FP32)
-    std::vector<float> leafv(4 * (size_t)n_pos, 0.f);
-    for (int64_t j = p->level_start[0]; j < p->level_start[1]; ++j) {
-        const hh::DNode& L = dn[j];
-        for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
-            const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
-                        vz = (float)(L.cz - mem_pos[3 * q + 2]);
-            leafv[4 * q] = vx;
-            leafv[4 * q + 1] = vy;
-            leafv[4 * q + 2] = vz;
-            leafv[4 * q + 3] = 0.5f * std::fmaf(vx, vx, std::fmaf(vy, vy, vz * vz));
+    // members relative to the centre of their node at each non-root level:
+    // v = centre - p' and |v|^2 / 2 (FP32), level-major
+    const int n_vec_levels = std::max(1, p->n_levels - 1);
+    std::vector<float> nodev(4 * (size_t)n_pos * (size_t)n_vec_levels, 0.f);
+    for (int l = 0; l + 1 < p->n_levels; ++l) {
+        float* out_l = nodev.data() + 4 * (size_t)n_pos * (size_t)l;
+        for (int64_t j = p->level_start[l]; j < p->level_start[l + 1]; ++j) {
+            const hh::DNode& L = dn[j];
+            for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
+                const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
+                            vz = (float)(L.cz - mem_pos[3 * q + 2]);
+                out_l[4 * q] = vx;
+                out_l[4 * q + 1] = vy;
+                out_l[4 * q + 2] = vz;
+                out_l[4 * q + 3] = 0.5f * std::fmaf(vx, vx, std::fmaf(vy, vy, vz * vz));
+            }
         }
     }
     std::vector<float> tw = hh::twiddle_table(p->n_fft);
@@ -283,7 +289,7 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     HH_TRY(dev_alloc(p, &p->d_tile_off, sizeof(int64_t) * p->tile_off.size()));
     HH_TRY(dev_alloc(p, &p->d_mem_pos, sizeof(double) * mem_pos.size()));
     HH_TRY(dev_alloc(p, &p->d_perm, sizeof(int64_t) * n_pos));
-    HH_TRY(dev_alloc(p, &p->d_leafv, sizeof(float) * leafv.size()));
+    HH_TRY(dev_alloc(p, &p->d_nodev, sizeof(float) * nodev.size()));
     HH_TRY(dev_alloc(p, &p->d_prof, 16 * (size_t)n_pos * (size_t)p->gate_n));
     HH_TRY(dev_alloc(p, &p->d_prof2, 8 * (size_t)n_pos * (size_t)((p->gate_n + 2) & ~(int64_t)1)));
     if (p->max_pool > 0) {
@@ -299,6 +305,21 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         }
         if (tiles > 0) HH_TRY(dev_alloc(p, &p->d_tile_ref, sizeof(float) * 16 * (size_t)tiles));
     }
+    if (p->n_levels > 1) {  // deferred-fallback queue, sized for the widest merge level
+        int64_t segs = 1, widest = 1;
+        for (int l = 1; l < p->n_levels; ++l) {
+            const int64_t nch = p->nodes[p->level_start[l]].nchild;
+            segs = std::max(segs, p->level_tiles[l] * nch);
+            widest = std::max(widest, p->level_samples[l] * nch);
+        }
+        p->fb_seg_cap = segs;  // at most one segment per (tile, child): never full
+        p->fb_rec_cap = std::min<int64_t>(std::max<int64_t>(widest / 4, 1 << 16), (int64_t)1 << 25);
+        HH_TRY(dev_alloc(p, &p->d_fb_segs, sizeof(hh::FbSeg) * (size_t)p->fb_seg_cap));
+        HH_TRY(dev_alloc(p, &p->d_fb_recs, sizeof(hh::FbRec) * (size_t)p->fb_rec_cap));
+        HH_TRY(dev_alloc(p, &p->d_fb_vals, 8 * (size_t)p->fb_rec_cap));
+        HH_TRY(dev_alloc(p, &p->d_fb_fixes, sizeof(hh::FbFix) * (size_t)p->fb_rec_cap));
+        HH_TRY(dev_alloc(p, &p->d_fb_counts, 32));
+    }
     if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, (size_t)p->need_total));
     if (p->xyz_total > 0) HH_TRY(dev_alloc(p, &p->d_xyz, 16 * (size_t)p->xyz_total));
     HH_TRY(dev_alloc(p, &p->d_twiddle, sizeof(float) * tw.size()));
@@ -311,7 +332,7 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         HH_TRY(upload(p->d_tile_off, p->tile_off.data(), sizeof(int64_t) * p->tile_off.size(), s));
     HH_TRY(upload(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), s));
     HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
-    HH_TRY(upload(p->d_leafv, leafv.data(), sizeof(float) * leafv.size(), s));
+    HH_TRY(upload(p->d_nodev, nodev.data(), sizeof(float) * nodev.size(), s));
     HH_TRY(upload(p->d_twiddle, tw.data(), sizeof(float) * tw.size(), s));
     HH_TRY(upload(p->d_wtable, p->wtable.data(), sizeof(float) * p->wtable.size(), s));
     cudaError_t e = cudaStreamSynchronize(s);
@@ -423,11 +444,15 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
         HH_LAUNCH(hh::launch_stage0(p, kc, cuda_stream));
         for (int l = 1; l + 1 < p->n_levels; ++l) {
             HH_MARK(HH_STAGE_MERGE, l);
+            HH_CUDA(cudaMemsetAsync(p->d_fb_counts, 0, 32, s));
             HH_LAUNCH(hh::launch_merge(p, kc, l, cuda_stream));
+            HH_LAUNCH(hh::launch_deferred(p, kc, l, p->d_pool[l & 1], cuda_stream));
         }
     }
     HH_MARK(HH_STAGE_FINAL, p->n_levels - 1);
+    if (p->n_levels > 1) HH_CUDA(cudaMemsetAsync(p->d_fb_counts, 0, 32, s));
     HH_LAUNCH(hh::launch_final(p, kc, image, cuda_stream));
+    if (p->n_levels > 1) HH_LAUNCH(hh::launch_deferred(p, kc, p->n_levels - 1, image, cuda_stream));
     if (host_img) {
         HH_MARK(HH_STAGE_D2H, -1);
         HH_CUDA(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));

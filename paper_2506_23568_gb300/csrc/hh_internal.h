@@ -50,6 +50,32 @@ struct TileMap {
     int32_t ntx, nty;      // voxel level: tiles along x and y
 };
 
+// Deferred exact fallbacks of one merge level: groups of points of one child
+// (segments) whose member sums stage 0's kernel evaluates, and per output the
+// records to add (fixes), in child order.
+struct FbSeg {
+    int32_t node, count;  // child node, points
+    int64_t rec0;         // first record
+};
+struct FbRec {
+    float x, y, z;  // point in the child's frame
+    float c, s;     // exp(j theta): the remodulation of the child's term
+    float pad;
+};
+struct FbFix {
+    int64_t out;     // output sample (level pool or image voxel)
+    int32_t rec[4];  // the deferred record of child 0..3, -1 when none
+};
+struct FbQueue {
+    FbSeg* segs;
+    FbRec* recs;
+    void* vals;                   // float2 per record: exp(j theta) g_child(point)
+    FbFix* fixes;
+    unsigned long long* counts;   // [0] segments, [1] records, [2] fixes
+    int64_t rec_cap;
+};
+constexpr int kDeferMin = 32;     // smaller groups are evaluated where they arise
+
 // Host-side node record (the plan's own, FP64).
 struct HNode {
     int level = 0, depth = 0, t = 0;
@@ -85,7 +111,8 @@ struct KConst {
 // Device counters (int64): see hhffbp_plan_counters.
 // CNT_NEEDED + level: samples evaluated at that level (the root: voxels).
 enum Counter { CNT_FALLBACK = 0, CNT_INFEASIBLE = 1, CNT_NEWTON_FAIL = 2, CNT_GATE_MISS = 3, CNT_ERROR = 4,
-               CNT_FALLBACK_UPDATES = 5, CNT_NEEDED = 8, CNT_N = 8 + 2 * kMaxLevels };
+               CNT_FALLBACK_UPDATES = 5, CNT_FB_DEFERRED = 6, CNT_FB_OVERFLOW = 7, CNT_NEEDED = 8,
+               CNT_N = 8 + 2 * kMaxLevels };
 
 }  // namespace hh
 
@@ -118,7 +145,7 @@ struct hh_plan {
     void* d_tile_off = nullptr;  // int64 copy of tile_off
     void* d_mem_pos = nullptr;   // double[n_pos][3], tree order
     void* d_perm = nullptr;      // int64[n_pos]
-    void* d_leafv = nullptr;     // float4[n_pos], tree order: leaf centre - p', |.|^2 / 2 (FP32)
+    void* d_nodev = nullptr;     // float4[L-1][n_pos], tree order: node centre - p', |.|^2 / 2 (FP32)
     void* d_prof = nullptr;      // float4[n_pos][gate_n] (P[m], P[m+1] - P[m]), tree order
     void* d_prof2 = nullptr;     // float2[n_pos][(gate_n + 2) & ~1] P[m] alone (stage-0 windows)
     void* d_pool[2] = {nullptr, nullptr};
@@ -129,6 +156,13 @@ struct hh_plan {
     void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
     void* d_tile_ref = nullptr;      // float[16] warm start per launch tile of levels 0..L-2
     std::vector<int64_t> tile_ref_base;  // per level: first tile in d_tile_ref
+    // deferred-fallback queue (one merge level at a time)
+    void* d_fb_segs = nullptr;
+    void* d_fb_recs = nullptr;
+    void* d_fb_vals = nullptr;
+    void* d_fb_fixes = nullptr;
+    void* d_fb_counts = nullptr;
+    int64_t fb_seg_cap = 0, fb_rec_cap = 0;
     std::vector<int64_t> need_base;  // per level: first sample in d_need
     std::vector<int64_t> xyz_base;   // per level: first sample in d_xyz (levels >= 1)
     int64_t need_total = 0, xyz_total = 0;
@@ -162,6 +196,7 @@ int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);
 int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_tile_refs(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_stage0(const hh_plan* p, const KConst& kc, void* stream);
+int launch_deferred(const hh_plan* p, const KConst& kc, int level, void* out, void* stream);
 int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_final(const hh_plan* p, const KConst& kc, void* d_image, void* stream);
 int launch_preimage_probe(const hh_plan* p, const KConst& kc, int node, const double* d_tgt, int64_t n, double* d_out,

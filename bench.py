@@ -44,7 +44,11 @@ PLAN_CFG = {"large": dict(leaf_size=256, eta=1.75), "mid": dict(leaf_size=256, e
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
 # benchmark command on the large workload (profiles/launches_large_bench.md); valid for the
 # kernels and plan they were taken with, reported as null otherwise.
-TRAFFIC = {}
+TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.75, 6): 1039.4e6,
+           ("large", "merge", 1, 256, 1.75, 6): 2031.1e6,
+           ("large", "merge", 2, 256, 1.75, 6): 1261.3e6,
+           ("large", "merge", 3, 256, 1.75, 6): 1255.4e6,
+           ("large", "final", 4, 256, 1.75, 6): 2474.2e6}
 
 # Algorithmic work per unit ("Measurement"):
 BPA_FLOP, BPA_MUFU = 25.0, 3.0            # per (voxel, position) update

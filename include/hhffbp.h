@@ -134,7 +134,10 @@ int hhffbp_form_image(const hh_plan* plan, const void* echo_c64, void* image_c64
  * counters of the last form_image: out[0] exact-fallback evaluations, out[1]
  * infeasible lattice samples, out[2] preimage solver failures, out[3] range
  * lookups outside the stored gate (must be 0), out[4] other kernel errors (must
- * be 0), out[5] position updates spent in exact fallbacks.  Returns HH_ERR_DEVICE_FLAG when out[3] or out[4] is non-zero.
+ * be 0), out[5] position updates spent in exact fallbacks, out[6] exact fallbacks
+ * evaluated after their merge (queued in groups), out[7] groups evaluated in place
+ * because the queue was full.  Returns HH_ERR_DEVICE_FLAG when out[3] or out[4] is
+ * non-zero.
  */
 int hhffbp_plan_counters(const hh_plan* plan, int64_t out[8]);
 

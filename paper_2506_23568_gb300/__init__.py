@@ -246,7 +246,8 @@ class Plan:
         out = np.zeros(8, np.int64)
         st = lib().hhffbp_plan_counters(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
         c = dict(fallbacks=int(out[0]), infeasible=int(out[1]), newton_fail=int(out[2]), gate_miss=int(out[3]),
-                 errors=int(out[4]), fallback_updates=int(out[5]))
+                 errors=int(out[4]), fallback_updates=int(out[5]), fallbacks_deferred=int(out[6]),
+                 queue_full=int(out[7]))
         _check(st, f"plan_counters {c}")
         return c
 

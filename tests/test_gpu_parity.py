@@ -66,6 +66,21 @@ def test_hhffbpa_matches_oracle(hh, name, cfg):
         assert oracle.nrmse_db(img.cpu().numpy(), bpa) < -30
 
 
+def test_deferred_fallbacks_match_oracle(hh):
+    """A plan whose exact fallbacks come in large groups (evaluated after the merge by the
+    leaf kernel and added per output in child order) against the oracle."""
+    s, e = _scene("tiny")
+    cfg = dict(leaf_size=64, eta=1.75)
+    plan = hh.Plan(s.traj, s.freqs, s.grid, **cfg)
+    img = plan.form_image(e)
+    cnt = plan.counters()
+    assert cnt["fallbacks_deferred"] > 0 and cnt["queue_full"] == 0, cnt
+    ref, st = oracle.Plan(s.traj, s.freqs, s.grid, **cfg).hhffbpa(e.cpu().numpy())
+    assert _rel(img, ref.reshape(s.grid.shape)) < REL_TOL
+    again = plan.form_image(e).clone()
+    assert torch.equal(img, again)  # deferred terms are added in a fixed order
+
+
 def test_single_level_is_bpa(hh):
     s, e = _scene("small")
     plan = hh.Plan(s.traj, s.freqs, s.grid, leaf_size=10 ** 6)

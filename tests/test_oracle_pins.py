@@ -232,7 +232,7 @@ def test_preimage_round_trip():
 
 
 # --------------------------------------------------------------------------- interpolation kernel
-@pytest.mark.parametrize("taps,eta", [(4, 2.0), (6, 2.0), (6, 1.75)])
+@pytest.mark.parametrize("taps,eta", [(4, 2.0), (6, 2.0), (6, 1.75), (6, 1.6)])
 def test_ls_weights_identity_and_band(taps, eta):
     tau = np.linspace(0, 1, 41)
     w = oracle.ls_weights(taps, eta, tau)
@@ -250,7 +250,7 @@ def test_ls_weights_identity_and_band(taps, eta):
         np.testing.assert_allclose(wi, h_ref, atol=2e-4)
         # in-band tones are reproduced to the least-squares level
         err = np.abs(A @ wi - rhs)
-        assert err.max() < {(4, 2.0): 0.06, (6, 2.0): 0.01, (6, 1.75): 0.025}[(taps, eta)]
+        assert err.max() < {(4, 2.0): 0.06, (6, 2.0): 0.01, (6, 1.75): 0.025, (6, 1.6): 0.04}[(taps, eta)]
 
 
 # --------------------------------------------------------------------------- plan

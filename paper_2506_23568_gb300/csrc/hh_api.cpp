@@ -126,7 +126,7 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
-                     &p->d_twiddle, &p->d_wtable, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
+                     &p->d_twiddle, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
                      &p->d_need, &p->d_xyz, &p->d_nodev, &p->d_tile_ref, &p->d_prof2,
                      &p->d_fb_segs, &p->d_fb_recs, &p->d_fb_vals, &p->d_fb_fixes, &p->d_fb_counts};
     for (void** b : bufs)
@@ -323,7 +323,6 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, (size_t)p->need_total));
     if (p->xyz_total > 0) HH_TRY(dev_alloc(p, &p->d_xyz, 16 * (size_t)p->xyz_total));
     HH_TRY(dev_alloc(p, &p->d_twiddle, sizeof(float) * tw.size()));
-    HH_TRY(dev_alloc(p, &p->d_wtable, sizeof(float) * p->wtable.size()));
     HH_TRY(dev_alloc(p, &p->d_counters, sizeof(int64_t) * hh::CNT_N));
     HH_TRY(dev_alloc(p, &p->d_echo_stage, 8 * (size_t)n_pos * (size_t)n_f));
     HH_TRY(dev_alloc(p, &p->d_image_stage, 8 * (size_t)n_vox));
@@ -334,7 +333,6 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
     HH_TRY(upload(p->d_nodev, nodev.data(), sizeof(float) * nodev.size(), s));
     HH_TRY(upload(p->d_twiddle, tw.data(), sizeof(float) * tw.size(), s));
-    HH_TRY(upload(p->d_wtable, p->wtable.data(), sizeof(float) * p->wtable.size(), s));
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         free_device(p);

@@ -13,7 +13,6 @@ namespace hh {
 constexpr double kC = 299792458.0;  // m/s
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxLevels = 32;
-constexpr int kTableSteps = 512;    // interpolation weight table: tau = j / kTableSteps (12 KiB at 6 taps)
 
 // Device copy of a materialised node (every node of every level, root last).
 // Lattice sample (iu, iv, in) of a node sits at (u, v, n) = lo + (iu, iv, in) / eta
@@ -33,6 +32,17 @@ struct DNode {
     int32_t nchild;
     int32_t pad_;
     int64_t pool_off;      // first sample in the node's level pool
+};
+
+// Interpolation weights as polynomials of x = 2 tau - 1 (tau the fractional
+// index, in [0, 1)), degree 8, in even and odd parts per tap pair: with
+// o_q = q - (taps/2 - 1) the tap offsets, w_q(x) = E_q(x^2) + x O_q(x^2) and
+// w_{taps-1-q}(x) = E_q(x^2) - x O_q(x^2) for q < taps/2 (the least-squares
+// weights satisfy w_{taps-1-q}(tau) = w_q(1 - tau)).  Coefficients lowest first.
+constexpr int kPolyPairs = 3;  // taps / 2 for taps <= 6
+struct WPoly {
+    float e[kPolyPairs][5];
+    float o[kPolyPairs][4];
 };
 
 // Launch tiles: 8 x 8 x 4 lattice samples (u, v, n) of one node, or 8 x 8 x 4 voxels (x, y, z).
@@ -136,7 +146,7 @@ struct hh_plan {
     std::vector<int64_t> level_tiles;        // launch tiles per level (root: voxel tiles)
     std::vector<int64_t> tile_off;           // per-node first tile, all non-root levels concatenated
     std::vector<int64_t> tile_off_base;      // per level: first entry in tile_off
-    std::vector<float> wtable;               // (kTableSteps + 1) x taps
+    hh::WPoly wpoly{};                       // interpolation weights (polynomials)
     int64_t max_pool = 0;
     // device state
     bool on_device = false;
@@ -150,7 +160,6 @@ struct hh_plan {
     void* d_prof2 = nullptr;     // float2[n_pos][(gate_n + 2) & ~1] P[m] alone (stage-0 windows)
     void* d_pool[2] = {nullptr, nullptr};
     void* d_twiddle = nullptr;   // float2[2 n_fft]
-    void* d_wtable = nullptr;
     void* d_counters = nullptr;  // int64[CNT_N]
     void* d_need = nullptr;      // uint8 per lattice sample of every non-root level (need_base offsets)
     void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
@@ -185,7 +194,7 @@ int build_host_plan(hh_plan* p);
 void range_constants(const double* freqs, int n_f, int range_os, double* kmin, double* kmax, double* kc,
                      double* dk, int* n_fft, double* dR);
 std::vector<float> twiddle_table(int n_fft);
-std::vector<float> weight_table(int taps, double eta);
+WPoly weight_poly(int taps, double eta);
 
 // hh_kernels.cu (launch wrappers; return cudaError_t as int)
 int launch_rc(const void* echo, const int64_t* d_perm, int64_t n_pos, int n_f, int n_fft, int64_t gate0,

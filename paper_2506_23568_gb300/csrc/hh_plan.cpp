@@ -252,42 +252,69 @@ std::vector<float> twiddle_table(int n_fft) {
     return t;
 }
 
+// Solves the n x n system A x = b in place (Gauss-Jordan, partial pivoting);
+// a is row-major n x (n + 1) with b in the last column, x left there.
+static void solve_augmented(std::vector<double>& a, int n) {
+    const int w = n + 1;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(a[r * w + c]) > std::fabs(a[piv * w + c])) piv = r;
+        if (piv != c)
+            for (int j = 0; j <= n; ++j) std::swap(a[c * w + j], a[piv * w + j]);
+        const double d = a[c * w + c];
+        for (int j = 0; j <= n; ++j) a[c * w + j] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = a[r * w + c];
+            for (int j = 0; j <= n; ++j) a[r * w + j] -= f * a[c * w + j];
+        }
+    }
+}
+
 // Least-squares fractional-delay weights for a flat spectrum on |f| <= 1/(2 eta)
 // cycles/sample (the unit box sampled at density eta): taps at offsets
 // -(T/2-1) .. T/2, h(tau) = G^-1 r(tau), G_ij = sinc((o_i - o_j)/eta),
-// r_i = sinc((o_i - tau)/eta).  Tabulated at tau = j / kTableSteps.
-std::vector<float> weight_table(int taps, double eta) {
+// r_i = sinc((o_i - tau)/eta).
+static void ls_weights(int taps, double eta, double tau, double* h) {
     auto sinc = [](double x) { return x == 0.0 ? 1.0 : std::sin(kPi * x) / (kPi * x); };
-    int o0 = -(taps / 2 - 1);
-    std::vector<double> G((size_t)taps * taps);
-    for (int i = 0; i < taps; ++i)
-        for (int j = 0; j < taps; ++j) G[i * taps + j] = sinc((double)(i - j) / eta);
-    std::vector<float> out((size_t)(kTableSteps + 1) * taps);
-    std::vector<double> M((size_t)taps * (taps + 1));
-    for (int s = 0; s <= kTableSteps; ++s) {
-        double tau = (double)s / kTableSteps;
-        for (int i = 0; i < taps; ++i) {
-            for (int j = 0; j < taps; ++j) M[i * (taps + 1) + j] = G[i * taps + j];
-            M[i * (taps + 1) + taps] = sinc(((double)(o0 + i) - tau) / eta);
-        }
-        // Gauss-Jordan with partial pivoting
-        for (int c = 0; c < taps; ++c) {
-            int piv = c;
-            for (int r = c + 1; r < taps; ++r)
-                if (std::fabs(M[r * (taps + 1) + c]) > std::fabs(M[piv * (taps + 1) + c])) piv = r;
-            if (piv != c)
-                for (int j = 0; j <= taps; ++j) std::swap(M[c * (taps + 1) + j], M[piv * (taps + 1) + j]);
-            double d = M[c * (taps + 1) + c];
-            for (int j = 0; j <= taps; ++j) M[c * (taps + 1) + j] /= d;
-            for (int r = 0; r < taps; ++r) {
-                if (r == c) continue;
-                double f = M[r * (taps + 1) + c];
-                for (int j = 0; j <= taps; ++j) M[r * (taps + 1) + j] -= f * M[c * (taps + 1) + j];
-            }
-        }
-        for (int i = 0; i < taps; ++i) out[(size_t)s * taps + i] = (float)M[i * (taps + 1) + taps];
+    const int o0 = -(taps / 2 - 1);
+    std::vector<double> a((size_t)taps * (taps + 1));
+    for (int i = 0; i < taps; ++i) {
+        for (int j = 0; j < taps; ++j) a[i * (taps + 1) + j] = sinc((double)(i - j) / eta);
+        a[i * (taps + 1) + taps] = sinc(((double)(o0 + i) - tau) / eta);
     }
-    return out;
+    solve_augmented(a, taps);
+    for (int i = 0; i < taps; ++i) h[i] = a[i * (taps + 1) + taps];
+}
+
+// The weights as degree-8 polynomials of x = 2 tau - 1: interpolation of
+// h_q(tau) at the 9 Chebyshev nodes of [-1, 1] (within about 1e-7 of the exact
+// weights everywhere, the FP32 rounding level), split into even and odd parts.
+WPoly weight_poly(int taps, double eta) {
+    constexpr int kDeg = 8, kN = kDeg + 1;
+    WPoly wp{};
+    std::vector<double> h((size_t)kN * taps);
+    double xs[kN];
+    for (int k = 0; k < kN; ++k) {
+        xs[k] = std::cos((2 * k + 1) * kPi / (2 * kN));
+        ls_weights(taps, eta, 0.5 * (xs[k] + 1.0), &h[(size_t)k * taps]);
+    }
+    for (int q = 0; q < taps / 2 && q < kPolyPairs; ++q) {
+        std::vector<double> a((size_t)kN * (kN + 1));  // Vandermonde system for the monomial coefficients
+        for (int k = 0; k < kN; ++k) {
+            double xp = 1.0;
+            for (int j = 0; j < kN; ++j, xp *= xs[k]) a[k * (kN + 1) + j] = xp;
+            a[k * (kN + 1) + kN] = h[(size_t)k * taps + q];
+        }
+        solve_augmented(a, kN);
+        for (int j = 0; j < kN; ++j) {
+            const float c = (float)a[j * (kN + 1) + kN];
+            if (j % 2 == 0) wp.e[q][j / 2] = c;
+            else wp.o[q][j / 2] = c;
+        }
+    }
+    return wp;
 }
 
 int build_host_plan(hh_plan* p) {
@@ -502,7 +529,7 @@ int build_host_plan(hh_plan* p) {
         p->level_tiles[p->n_levels - 1] = (int64_t)((g.nx + kTile0 - 1) / kTile0) * ((g.ny + kTile1 - 1) / kTile1) *
                                           ((g.nz + kTile2 - 1) / kTile2);
     }
-    p->wtable = weight_table(cfg.taps, cfg.eta);
+    p->wpoly = weight_poly(cfg.taps, cfg.eta);
     return HH_OK;
 }
 

@@ -320,7 +320,7 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         HH_TRY(dev_alloc(p, &p->d_fb_fixes, sizeof(hh::FbFix) * (size_t)p->fb_rec_cap));
         HH_TRY(dev_alloc(p, &p->d_fb_counts, 32));
     }
-    if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, (size_t)p->need_total));
+    if (p->need_total > 0) HH_TRY(dev_alloc(p, &p->d_need, sizeof(uint32_t) * (size_t)p->need_total));
     if (p->xyz_total > 0) HH_TRY(dev_alloc(p, &p->d_xyz, 16 * (size_t)p->xyz_total));
     HH_TRY(dev_alloc(p, &p->d_twiddle, sizeof(float) * tw.size()));
     HH_TRY(dev_alloc(p, &p->d_counters, sizeof(int64_t) * hh::CNT_N));
@@ -431,7 +431,7 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
         // top-down: which lattice samples the image needs (the footprints of needed points)
         HH_MARK(HH_STAGE_NEED_FINAL, p->n_levels - 1);
         for (int l = 0; l + 1 < p->n_levels; ++l) HH_LAUNCH(hh::launch_tile_refs(p, kc, l, cuda_stream));
-        HH_CUDA(cudaMemsetAsync(p->d_need, 0, (size_t)p->need_total, s));
+        HH_CUDA(cudaMemsetAsync(p->d_need, 0, sizeof(uint32_t) * (size_t)p->need_total, s));
         HH_LAUNCH(hh::launch_need_final(p, kc, cuda_stream));
         for (int l = p->n_levels - 2; l >= 1; --l) {
             HH_MARK(HH_STAGE_NEED_LEVEL, l);

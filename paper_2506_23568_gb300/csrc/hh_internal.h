@@ -47,6 +47,9 @@ struct WPoly {
 
 // Launch tiles: 8 x 8 x 4 lattice samples (u, v, n) of one node, or 8 x 8 x 4 voxels (x, y, z).
 constexpr int kTile0 = 8, kTile1 = 8, kTile2 = 4;
+// Need masks: bit ((b mod 8) * 4 + c mod 4) of word (a mod 8) of a launch tile's
+// eight 32-bit words marks lattice sample (a, b, c) as needed.
+constexpr int kNeedWords = 8;
 // A launch tile: a box of lattice samples of one node, or a box of voxels.
 struct DTile {
     int32_t node;
@@ -161,7 +164,7 @@ struct hh_plan {
     void* d_pool[2] = {nullptr, nullptr};
     void* d_twiddle = nullptr;   // float2[2 n_fft]
     void* d_counters = nullptr;  // int64[CNT_N]
-    void* d_need = nullptr;      // uint8 per lattice sample of every non-root level (need_base offsets)
+    void* d_need = nullptr;      // uint32[8] bit mask per launch tile of every non-root level (need_base offsets)
     void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
     void* d_tile_ref = nullptr;      // float[16] warm start per launch tile of levels 0..L-2
     std::vector<int64_t> tile_ref_base;  // per level: first tile in d_tile_ref
@@ -172,7 +175,7 @@ struct hh_plan {
     void* d_fb_fixes = nullptr;
     void* d_fb_counts = nullptr;
     int64_t fb_seg_cap = 0, fb_rec_cap = 0;
-    std::vector<int64_t> need_base;  // per level: first sample in d_need
+    std::vector<int64_t> need_base;  // per level: first word in d_need
     std::vector<int64_t> xyz_base;   // per level: first sample in d_xyz (levels >= 1)
     int64_t need_total = 0, xyz_total = 0;
     void* d_echo_stage = nullptr;   // complex64[n_pos][n_f] for host echoes

@@ -457,8 +457,6 @@ int build_host_plan(hh_plan* p) {
     p->xyz_base.assign(p->n_levels, 0);
     p->need_total = p->xyz_total = 0;
     for (int l = 0; l + 1 < p->n_levels; ++l) {
-        p->need_base[l] = p->need_total;
-        p->need_total += p->level_samples[l];
         if (l >= 1) {
             p->xyz_base[l] = p->xyz_total;
             p->xyz_total += p->level_samples[l];
@@ -528,6 +526,11 @@ int build_host_plan(hh_plan* p) {
         const hh_grid& g = p->grid;
         p->level_tiles[p->n_levels - 1] = (int64_t)((g.nx + kTile0 - 1) / kTile0) * ((g.ny + kTile1 - 1) / kTile1) *
                                           ((g.nz + kTile2 - 1) / kTile2);
+    }
+    // need masks: one bit per lattice sample, 256 bits (eight words) per launch tile
+    for (int l = 0; l + 1 < p->n_levels; ++l) {
+        p->need_base[l] = p->need_total;
+        p->need_total += kNeedWords * p->level_tiles[l];
     }
     p->wpoly = weight_poly(cfg.taps, cfg.eta);
     return HH_OK;

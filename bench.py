@@ -45,11 +45,11 @@ PLAN_CFG = {"large": dict(leaf_size=256, eta=1.6), "mid": dict(leaf_size=256, et
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
 # benchmark command on the large workload (profiles/launches_large_bench.md); valid for the
 # kernels and plan they were taken with, reported as null otherwise.
-TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.75, 6): 1039.4e6,
-           ("large", "merge", 1, 256, 1.75, 6): 2031.1e6,
-           ("large", "merge", 2, 256, 1.75, 6): 1261.3e6,
-           ("large", "merge", 3, 256, 1.75, 6): 1255.4e6,
-           ("large", "final", 4, 256, 1.75, 6): 2474.2e6}
+TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.6, 6): 856.1e6,
+           ("large", "merge", 1, 256, 1.6, 6): 1804.8e6,
+           ("large", "merge", 2, 256, 1.6, 6): 1090.1e6,
+           ("large", "merge", 3, 256, 1.6, 6): 995.8e6,
+           ("large", "final", 4, 256, 1.6, 6): 1890.8e6}
 
 # Algorithmic work per unit ("Measurement"):
 BPA_FLOP, BPA_MUFU = 25.0, 3.0            # per (voxel, position) update
@@ -209,13 +209,14 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     img = torch.empty(grid.shape, dtype=torch.complex64, device="cuda")
     bimg = torch.empty_like(img)
 
     def step(timed):
         ev[0].record(stream)
         plan = hh.Plan(s.traj, s.freqs, grid, **cfg)
+        ev[4].record(stream)  # the plan is built (its constructor synchronises the stream)
         plan.profile(True)  # CUDA events around each stage, on the launching stream
         plan.form_image(echo, out=img)
         ev[1].record(stream)
@@ -231,7 +232,7 @@ def run_gpu(args):
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    t_hh, t_bpa, t_step, errs, stage_runs = [], [], [], [], []
+    t_hh, t_bpa, t_step, t_plan, errs, stage_runs = [], [], [], [], [], []
     barrier()
     g0 = torch.cuda.Event(enable_timing=True)
     g1 = torch.cuda.Event(enable_timing=True)
@@ -240,6 +241,7 @@ def run_gpu(args):
         plan, err = step(True)
         torch.cuda.synchronize()
         t_hh.append(ev[0].elapsed_time(ev[1]))
+        t_plan.append(ev[0].elapsed_time(ev[4]))
         t_bpa.append(ev[1].elapsed_time(ev[2]))
         t_step.append(ev[0].elapsed_time(ev[3]))
         errs.append(float(err))
@@ -337,9 +339,10 @@ def run_gpu(args):
         "roofline": {"kernel": f'{dom["stage"]}(level {dom["level"]})', "bound": d_bound, "achieved": d_ach,
                      "peak": d_peak, "unit": d_unit, "frac": d_frac,
                      "traffic": TRAFFIC.get((wl, dom["stage"], dom["level"], cfg.get("leaf_size"),
-                                             plan.config.eta, plan.config.taps)),
+                                             round(plan.config.eta, 4), plan.config.taps)),
                      "peak_source": f'{peaks["source"]} ({MUFU_PER_SM_CLK:g} SFU/clk/SM, {FP32_PER_SM_CLK:g} '
                                     f'FLOP/clk/SM x 152 SMs at the sampled {clk_mhz:.0f} MHz)'},
+        "plan_ms": statistics.mean(t_plan),
         "roofline_pipeline": {"roofline_ms": roof_ms, "kernels_ms": hh_kernel_ms,
                               "frac": roof_ms / hh_kernel_ms if hh_kernel_ms else None,
                               "frac_incl_plan": roof_ms / mean_hh},

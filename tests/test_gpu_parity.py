@@ -159,6 +159,31 @@ def test_mid_sampled_parity(hh):
     assert oracle.nrmse_db(img.cpu().numpy(), bimg.cpu().numpy()) < -30
 
 
+def test_large_sampled_parity_benchmark_plan(hh):
+    """Full-size large workload in the benchmark's launch configuration and plan (leaf 256,
+    eta 1.6, 6 taps): voxel clusters at the centre, an edge and a corner of the grid against
+    the oracle (demand-driven), a subset against the oracle's BPA-RC, and the whole volume
+    against the GPU's direct BPA (-30 dB)."""
+    s, e = _scene("large")
+    g = s.grid
+    cfg = dict(leaf_size=256, eta=1.6)
+    plan = hh.Plan(s.traj, s.freqs, g, **cfg)
+    img = plan.form_image(e)
+    cnt = plan.counters()
+    assert cnt["errors"] == 0 and cnt["gate_miss"] == 0 and cnt["queue_full"] == 0, cnt
+    ec = e.cpu().numpy()
+    idx = _clusters(g, [(256, 256, 64), (20, 300, 120), (500, 8, 3)])
+    ref, st = oracle.Plan(s.traj, s.freqs, g, **cfg).hhffbpa(ec, g.points(idx))
+    got = img.reshape(-1)[torch.as_tensor(idx, device=img.device)].cpu().numpy()
+    assert oracle.rel_l2(got.astype(np.complex128), ref) < REL_TOL, (cnt, st)
+    bimg = hh.bpa_form_image(s.traj, s.freqs, g, e)
+    bi = idx[::13]
+    bref = oracle.bpa_rc(s.traj, s.freqs, ec, g.points(bi))
+    bgot = bimg.reshape(-1)[torch.as_tensor(bi, device=img.device)].cpu().numpy()
+    assert oracle.rel_l2(bgot.astype(np.complex128), bref) < REL_TOL
+    assert oracle.nrmse_db(img.cpu().numpy(), bimg.cpu().numpy()) < -30
+
+
 @pytest.mark.parametrize("name,cfg", [("tiny", dict(leaf_size=64, taps=4)), ("large", dict(leaf_size=64))])
 def test_preimage_solver_matches_oracle(hh, name, cfg):
     """The device FP32 preimage solver against the FP64 oracle's on lattice targets of leaves

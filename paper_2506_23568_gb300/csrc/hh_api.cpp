@@ -269,20 +269,19 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     // v = centre - p' and |v|^2 / 2 (FP32), level-major
     const int n_vec_levels = std::max(1, p->n_levels - 1);
     std::vector<float> nodev(4 * (size_t)n_pos * (size_t)n_vec_levels, 0.f);
-    for (int l = 0; l + 1 < p->n_levels; ++l) {
-        float* out_l = nodev.data() + 4 * (size_t)n_pos * (size_t)l;
-        for (int64_t j = p->level_start[l]; j < p->level_start[l + 1]; ++j) {
-            const hh::DNode& L = dn[j];
-            for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
-                const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
-                            vz = (float)(L.cz - mem_pos[3 * q + 2]);
-                out_l[4 * q] = vx;
-                out_l[4 * q + 1] = vy;
-                out_l[4 * q + 2] = vz;
-                out_l[4 * q + 3] = 0.5f * std::fmaf(vx, vx, std::fmaf(vy, vy, vz * vz));
-            }
+    const int64_t n_vec_nodes = p->n_levels > 1 ? p->level_start[p->n_levels - 1] : 0;
+    hh::parallel_for(n_vec_nodes, n_pos >= 32768 ? 16 : 1, [&](int64_t j) {  // nodes of levels 0 .. L-2
+        float* out_l = nodev.data() + 4 * (size_t)n_pos * (size_t)p->nodes[j].level;
+        const hh::DNode& L = dn[j];
+        for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
+            const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
+                        vz = (float)(L.cz - mem_pos[3 * q + 2]);
+            out_l[4 * q] = vx;
+            out_l[4 * q + 1] = vy;
+            out_l[4 * q + 2] = vz;
+            out_l[4 * q + 3] = 0.5f * std::fmaf(vx, vx, std::fmaf(vy, vy, vz * vz));
         }
-    }
+    });
     std::vector<float> tw = hh::twiddle_table(p->n_fft);
     const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
     HH_TRY(dev_alloc(p, &p->d_nodes, sizeof(hh::DNode) * dn.size()));

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "../../include/hhffbp.h"
@@ -198,6 +199,8 @@ void range_constants(const double* freqs, int n_f, int range_os, double* kmin, d
                      double* dk, int* n_fft, double* dR);
 std::vector<float> twiddle_table(int n_fft);
 WPoly weight_poly(int taps, double eta);
+// Runs f(i) for i in [0, n) on up to `threads` host threads (i = t, t + T, ...).
+void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& f);
 
 // hh_kernels.cu (launch wrappers; return cudaError_t as int)
 int launch_rc(const void* echo, const int64_t* d_perm, int64_t n_pos, int n_f, int n_fft, int64_t gate0,

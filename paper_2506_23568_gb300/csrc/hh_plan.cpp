@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 #include <thread>
 
@@ -317,6 +318,22 @@ WPoly weight_poly(int taps, double eta) {
     return wp;
 }
 
+void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& f) {
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)threads, n}));
+    if (nt == 1) {
+        for (int64_t i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int64_t t = 1; t < nt; ++t)
+        pool.emplace_back([&f, n, nt, t]() {
+            for (int64_t i = t; i < n; i += nt) f(i);
+        });
+    for (int64_t i = 0; i < n; i += nt) f(i);
+    for (auto& th : pool) th.join();
+}
+
 int build_host_plan(hh_plan* p) {
     const hh_config& cfg = p->cfg;
     const int64_t n = p->n_pos;
@@ -341,25 +358,41 @@ int build_host_plan(hh_plan* p) {
     p->depth_leaves = D;
     p->perm.resize(n);
     std::iota(p->perm.begin(), p->perm.end(), (int64_t)0);
+    // node boundaries depend on the sizes alone
     std::vector<std::vector<int64_t>> bounds(D + 1);
     bounds[0] = {0, n};
     for (int d = 0; d < D; ++d) {
-        const int axis = d & 1;
         const std::vector<int64_t>& bd = bounds[d];
         std::vector<int64_t>& nb = bounds[d + 1];
-        nb.clear();
         for (size_t j = 0; j + 1 < bd.size(); ++j) {
-            int64_t b0 = bd[j], b1 = bd[j + 1], mid = b0 + (b1 - b0) / 2;
-            auto less = [&](int64_t u, int64_t v) {
-                double cu = T[3 * u + axis], cv = T[3 * v + axis];
-                return cu < cv || (cu == cv && u < v);
-            };
-            std::nth_element(p->perm.begin() + b0, p->perm.begin() + mid, p->perm.begin() + b1, less);
-            nb.push_back(b0);
-            nb.push_back(mid);
+            nb.push_back(bd[j]);
+            nb.push_back(bd[j] + (bd[j + 1] - bd[j]) / 2);
         }
         nb.push_back(n);
     }
+    // the selections: node j of depth d splits at its mid point; the two halves are
+    // independent, so subtrees below depth kSplitSpawn run on their own host threads
+    // (every range sees the same sequence of operations whichever thread runs it)
+    constexpr int kSplitSpawn = 4;
+    std::function<void(int, size_t)> split = [&](int d, size_t j) {
+        if (d >= D) return;
+        const int axis = d & 1;
+        const int64_t b0 = bounds[d][j], b1 = bounds[d][j + 1], mid = b0 + (b1 - b0) / 2;
+        auto less = [&](int64_t u, int64_t v) {
+            double cu = T[3 * u + axis], cv = T[3 * v + axis];
+            return cu < cv || (cu == cv && u < v);
+        };
+        std::nth_element(p->perm.begin() + b0, p->perm.begin() + mid, p->perm.begin() + b1, less);
+        if (d < kSplitSpawn && b1 - b0 >= 4096) {
+            std::thread left([&split, d, j]() { split(d + 1, 2 * j); });
+            split(d + 1, 2 * j + 1);
+            left.join();
+        } else {
+            split(d + 1, 2 * j);
+            split(d + 1, 2 * j + 1);
+        }
+    };
+    split(0, 0);
     // materialised depths: D, D - s, ..., (> 0), then the root
     const int step = cfg.merge_factor == 4 ? 2 : 1;
     std::vector<int> depths;
@@ -385,26 +418,30 @@ int build_host_plan(hh_plan* p) {
                 nd.child0 = p->level_start[l - 1] + j * f;
                 nd.nchild = f;
             }
-            double a = HUGE_VAL, b = -HUGE_VAL, e = HUGE_VAL, g = -HUGE_VAL;
-            double zs = 0;
-            nd.zmin = HUGE_VAL;
-            nd.zmax = -HUGE_VAL;
-            for (int64_t q = nd.begin; q < nd.end; ++q) {
-                const double* pp = T + 3 * p->perm[q];
-                a = std::min(a, pp[0]); b = std::max(b, pp[0]);
-                e = std::min(e, pp[1]); g = std::max(g, pp[1]);
-                nd.zmin = std::min(nd.zmin, pp[2]);
-                nd.zmax = std::max(nd.zmax, pp[2]);
-                zs += pp[2];
-            }
-            nd.zbar = zs / (double)(nd.end - nd.begin);
-            if (b - a < min_ext) { double c = 0.5 * (a + b); a = c - 0.5 * min_ext; b = c + 0.5 * min_ext; }
-            if (g - e < min_ext) { double c = 0.5 * (e + g); e = c - 0.5 * min_ext; g = c + 0.5 * min_ext; }
-            nd.rect[0] = a; nd.rect[1] = b; nd.rect[2] = e; nd.rect[3] = g;
             p->nodes.push_back(nd);
         }
     }
     p->level_start[p->n_levels] = (int64_t)p->nodes.size();
+    // member boxes and mean heights, one node per task
+    parallel_for((int64_t)p->nodes.size(), n >= 32768 ? 16 : 1, [&](int64_t k) {
+        HNode& nd = p->nodes[k];
+        double a = HUGE_VAL, b = -HUGE_VAL, e = HUGE_VAL, g = -HUGE_VAL;
+        double zs = 0;
+        nd.zmin = HUGE_VAL;
+        nd.zmax = -HUGE_VAL;
+        for (int64_t q = nd.begin; q < nd.end; ++q) {
+            const double* pp = T + 3 * p->perm[q];
+            a = std::min(a, pp[0]); b = std::max(b, pp[0]);
+            e = std::min(e, pp[1]); g = std::max(g, pp[1]);
+            nd.zmin = std::min(nd.zmin, pp[2]);
+            nd.zmax = std::max(nd.zmax, pp[2]);
+            zs += pp[2];
+        }
+        nd.zbar = zs / (double)(nd.end - nd.begin);
+        if (b - a < min_ext) { double c = 0.5 * (a + b); a = c - 0.5 * min_ext; b = c + 0.5 * min_ext; }
+        if (g - e < min_ext) { double c = 0.5 * (e + g); e = c - 0.5 * min_ext; g = c + 0.5 * min_ext; }
+        nd.rect[0] = a; nd.rect[1] = b; nd.rect[2] = e; nd.rect[3] = g;
+    });
 
     // ---- sampling grids: a uniform lattice in (u, v, n) per non-root node
     // (Sec. IV-A), covering the image of D plus a margin, with per-axis density

@@ -137,6 +137,24 @@ def _scene(name, rank):
     return s
 
 
+def reduce_over_ranks(dist, values, device):
+    """Max over ranks of each timing (the slowest rank sets the job's time); identity
+    without a process group."""
+    if dist is None:
+        return list(values)
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def per_volume_s(job_ms, ranks):
+    """Whole-job seconds per volume: every rank images one volume per step, so the job's
+    time per step is shared by `ranks` volumes."""
+    return job_ms / 1e3 / ranks
+
+
 def roofline_of(kind, ms, units, peaks, clk_mhz):
     """(achieved, peak, unit, bound, frac) for a kernel from its algorithmic work."""
     f = clk_mhz * 1e6
@@ -251,12 +269,8 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     total_ms = g0.elapsed_time(g1)
-    if dist is not None:
-        t = torch.tensor([total_ms, statistics.mean(t_hh), statistics.mean(t_bpa)], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, mean_hh, mean_bpa = t.tolist()
-    else:
-        mean_hh, mean_bpa = statistics.mean(t_hh), statistics.mean(t_bpa)
+    total_ms, mean_hh, mean_bpa = reduce_over_ranks(
+        dist, [total_ms, statistics.mean(t_hh), statistics.mean(t_bpa)], "cuda")
 
     # per-stage durations averaged over the timed steps
     stages = [(name, lev, statistics.mean(run[i][2] for run in stage_runs))
@@ -314,7 +328,7 @@ def run_gpu(args):
     n_launch = (5 * L - 3 if L > 1 else 2) + 2
     nr_db = 20 * math.log10(statistics.mean(errs))
     value = total_ms / 1e3 / args.steps  # whole step per volume (reported for the driver clock)
-    hh_s = mean_hh / 1e3 / ws
+    hh_s = per_volume_s(mean_hh, ws)
     line = {
         "metric": METRIC,
         "value": hh_s,

@@ -55,6 +55,7 @@ TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.6, 6): 826.3e6,
 BPA_FLOP, BPA_MUFU = 25.0, 3.0            # per (voxel, position) update
 MUFU_PER_SM_CLK = 16.0                    # SFU results per SM per clock (sm_100-class)
 FP32_PER_SM_CLK = 256.0                   # 128 FMA lanes x 2 FLOP
+SMEM_B_PER_SM_CLK = 128.0                 # shared-memory bytes per SM per clock (one wavefront)
 
 
 def _peaks():
@@ -193,7 +194,10 @@ def kernel_work(stages, plan, info, levels, cnt, grid, n_pos, n_f, taps):
             flop = interp * (4.0 * taps ** 3 + 100.0)
             mufu = interp * 11.0
             byts = 8.0 * levels[lev] + 8.0 * levels[lev - 1]
-        out.append(dict(stage=name, level=lev, ms=ms, flop=flop, mufu=mufu, bytes=byts))
+        # shared-memory reads of the separable interpolation: taps^3 complex64 samples per
+        # (sample, child); not part of the FP32 / MUFU / HBM roofline, reported beside it
+        smem = 8.0 * taps ** 3 * levels[lev] * plan["nchild"][lev] if name in ("merge", "final") else 0.0
+        out.append(dict(stage=name, level=lev, ms=ms, flop=flop, mufu=mufu, bytes=byts, smem=smem))
     return out
 
 
@@ -360,6 +364,11 @@ def run_gpu(args):
         "roofline_pipeline": {"roofline_ms": roof_ms, "kernels_ms": hh_kernel_ms,
                               "frac": roof_ms / hh_kernel_ms if hh_kernel_ms else None,
                               "frac_incl_plan": roof_ms / mean_hh},
+        "smem_merges": [{"stage": w["stage"], "level": w["level"], "achieved": w["smem"] / (w["ms"] * 1e-3) / 1e12,
+                         "peak": SMEM_B_PER_SM_CLK * 152 * clk_mhz * 1e6 / 1e12, "unit": "TB/s",
+                         "frac": w["smem"] / (w["ms"] * 1e-3) / (SMEM_B_PER_SM_CLK * 152 * clk_mhz * 1e6),
+                         "peak_source": f"derived ({SMEM_B_PER_SM_CLK:g} B/clk/SM x 152 SMs at {clk_mhz:.0f} MHz)"}
+                        for w in work if w["smem"] > 0],
         "roofline_bpa": {"bound": b_bound, "achieved": b_ach, "peak": b_peak, "unit": b_unit, "frac": b_frac,
                          "traffic": None},
         "counters": cnt,

@@ -1,5 +1,5 @@
 // Host planning for HHFFBPA: subarray tree, per-subarray (u, v, n) sampling
-// grids, range gate, launch tiles and interpolation tables (Sec. III, Sec. IV-A).
+// grids, range gate, launch tiles and interpolation weights (Sec. III, Sec. IV-A).
 // FP64 throughout; nothing here touches the GPU.
 #include <algorithm>
 #include <cmath>

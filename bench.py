@@ -45,11 +45,11 @@ PLAN_CFG = {"large": dict(leaf_size=256, eta=1.6), "mid": dict(leaf_size=256, et
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
 # benchmark command on the large workload (profiles/launches_large_bench.md); valid for the
 # kernels and plan they were taken with, reported as null otherwise.
-TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.6, 6): 823.5e6,
-           ("large", "merge", 1, 256, 1.6, 6): 1544.4e6,
-           ("large", "merge", 2, 256, 1.6, 6): 958.4e6,
-           ("large", "merge", 3, 256, 1.6, 6): 965.0e6,
-           ("large", "final", 4, 256, 1.6, 6): 1799.0e6}
+TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.6, 6): 823.7e6,
+           ("large", "merge", 1, 256, 1.6, 6): 1498.5e6,
+           ("large", "merge", 2, 256, 1.6, 6): 923.7e6,
+           ("large", "merge", 3, 256, 1.6, 6): 915.6e6,
+           ("large", "final", 4, 256, 1.6, 6): 1797.1e6}
 
 # Algorithmic work per unit ("Measurement"):
 BPA_FLOP, BPA_MUFU = 25.0, 3.0            # per (voxel, position) update

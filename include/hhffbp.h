@@ -189,6 +189,25 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
                    const hh_config* cfg, const void* echo_c64, void* image_c64, void* cuda_stream);
 
 /*
+ * bpa_traj_gradient -- gradient of a real loss of the direct BPA image with
+ * respect to the positions (the paper forms images only; this differentiates
+ * the sum of Eq. eq2_bpatimedomain term by term).  With g the image gradient
+ * (grad_image_c64, device complex64 [nz][ny][nx], dL = Re sum_p conj(g_p) df_p):
+ *   dL/dp'_i = sum_p Re[conj(g_p) exp(+j 2 k_c R_i) (j 2 k_c lerp_i + (P_i[m0+1] - P_i[m0]) / dR)]
+ *              (p'_i - p) / R_i,
+ * with R_i, m0, lerp_i as in bpa_form_image (the range profiles do not depend on
+ * the positions; the lerp is differentiated within its bin).  grad_traj:
+ * device float64 [n_pos][3], overwritten.  traj_xyz, freqs_hz: host float64;
+ * echo_c64: device or host complex64 [n_pos][n_f].  Only cfg->range_os is used.
+ * Workspace is allocated and freed stream-ordered.  Asynchronous on cuda_stream.
+ * Errors: HH_ERR_ARG (null pointers, host gradient buffers), HH_ERR_FREQ_NONUNIFORM,
+ * HH_ERR_OOM, HH_ERR_CUDA.
+ */
+int bpa_traj_gradient(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f,
+                      const hh_grid* grid, const hh_config* cfg, const void* echo_c64, const void* grad_image_c64,
+                      double* grad_traj, void* cuda_stream);
+
+/*
  * bpa_form_image_noalloc -- bpa_form_image for callers that cannot allocate
  * memory during the call.  The paper has no counterpart: it is an interface
  * variant of the same computation (Eqs. eq2_rangecompression and

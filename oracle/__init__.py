@@ -145,6 +145,32 @@ def bpa_rc(traj, freqs, echo, pts, os_r=16):
     return _cplx(out, (len(p),))
 
 
+def bpa_rc_traj_grad(traj, freqs, echo, pts, g, os_r=16):
+    """Gradient with respect to the positions of L = Re sum_p conj(g_p) f(p), f the BPA-RC
+    image (Eqs. eq2_rangecompression, eq2_bpatimedomain: f(p) = sum_i exp(+j 2 k_c R_i)
+    lerp(P_i, R_i / dR)) at the points pts, in FP64.  The range profiles do not depend on
+    the positions and the lerp is differentiated within its bin:
+    dL/dp'_i = sum_p Re[conj(g_p) exp(+j 2 k_c R) (j 2 k_c lerp + (P[m0+1] - P[m0]) / dR)] (p'_i - p) / R.
+    Returns float64[n_pos][3].  Plain numpy over all (position, point) pairs: small cases."""
+    t, p = _f64(traj), _f64(pts)
+    g = np.asarray(g, np.complex128).ravel()
+    n_fft, dR, kc, _ = rc_params(freqs, os_r)
+    d = t[:, None, :] - p[None, :, :]
+    R = np.sqrt((d * d).sum(-1))
+    mu = R / dR
+    m0 = np.floor(mu)
+    frac = mu - m0
+    m_lo = int(m0.min())
+    P = rc_window(echo, n_fft, m_lo, int(m0.max()) - m_lo + 2)
+    idx = (m0 - m_lo).astype(np.int64)
+    P0 = np.take_along_axis(P, idx, 1)
+    P1 = np.take_along_axis(P, idx + 1, 1)
+    lerp = P0 + frac * (P1 - P0)
+    E = np.exp(2j * kc * R) * (2j * kc * lerp + (P1 - P0) / dR)
+    a = (np.conj(g)[None, :] * E).real
+    return ((a / R)[:, :, None] * d).sum(axis=1)
+
+
 def keypoints(rect, zbar, kmin, kmax, p):
     """(k[7][3], Ts[3][3]) at point p for subarray rect = (a, b, e, g)."""
     r, pp = _f64(rect), _f64(p)

@@ -19,7 +19,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Grid", "Config", "Plan", "bpa_form_image", "bpa_form_image_noalloc", "lib", "LibraryError", "status_string", "SYMBOLS"]
+__all__ = ["Grid", "Config", "Plan", "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient",
+           "bpa_image_with_offsets", "lib", "LibraryError", "status_string", "SYMBOLS"]
 
 HH_OK = 0
 HH_ERR_ARG = 1
@@ -37,7 +38,8 @@ HH_FLAG_HOST_ONLY = 1
 SYMBOLS = ["hhffbp_default_config", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
            "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
            "hhffbp_plan_stage_times", "hhffbp_plan_preimages",
-           "bpa_form_image", "bpa_form_image_noalloc", "hhffbp_adjoint", "hh_status_string", "hh_last_cuda_error",
+           "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "hhffbp_adjoint", "hh_status_string",
+           "hh_last_cuda_error",
            "hh_release_cached_memory"]
 STAGE_NAMES = {0: "range_compression", 1: "need_final", 2: "need_level", 3: "leaf_subimages", 4: "merge",
                5: "final", 6: "h2d", 7: "d2h"}
@@ -105,6 +107,8 @@ def _declare(L):
     L.hhffbp_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32p, i32p, ctypes.c_int32, i32p]
     L.bpa_form_image.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
                                  ctypes.POINTER(hh_config), vp, vp, vp]
+    L.bpa_traj_gradient.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
+                                    ctypes.POINTER(hh_config), vp, vp, vp, vp]
     L.hhffbp_adjoint.argtypes = [vp, vp, vp, vp]
     L.hh_status_string.argtypes = [ctypes.c_int]
     L.hh_status_string.restype = ctypes.c_char_p
@@ -306,6 +310,63 @@ def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16):
                                 ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
            "bpa_form_image")
     return out
+
+
+def bpa_traj_gradient(traj, freqs, grid, echo, grad_image, out=None, stream=None, range_os=16):
+    """Gradient of a real loss of the direct BPA image with respect to the positions:
+    grad_image is the loss's gradient with respect to the image (complex64 CUDA tensor
+    [nz][ny][nx], torch's convention dL = Re sum conj(g) df); returns float64 [n_pos][3] on
+    the image's device."""
+    import torch
+
+    t, f = _f64(traj), _f64(freqs)
+    g = Grid.from_any(grid)
+    cfg = Config(range_os=range_os)
+    gi = grad_image.contiguous()
+    if gi.dtype != torch.complex64:
+        gi = gi.to(torch.complex64)
+    if out is None:
+        out = torch.empty((len(t), 3), dtype=torch.float64, device=gi.device)
+    _check(lib().bpa_traj_gradient(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
+                                   f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
+                                   ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(gi), _buffer_ptr(out),
+                                   _stream_ptr(stream)),
+           "bpa_traj_gradient")
+    return out
+
+
+def _bpa_offsets_function():
+    import torch
+
+    class _BPAOffsets(torch.autograd.Function):
+        """Direct BPA image of the positions traj + offsets; the backward pass is the
+        hand-written gradient kernel (bpa_traj_gradient)."""
+
+        @staticmethod
+        def forward(ctx, offsets, traj, freqs, grid, echo, range_os):
+            pos = np.asarray(traj, np.float64) + offsets.detach().cpu().numpy().astype(np.float64)
+            ctx.pos, ctx.freqs, ctx.grid, ctx.echo, ctx.range_os = pos, freqs, grid, echo, range_os
+            ctx.offsets_device = offsets.device
+            return bpa_form_image(pos, freqs, grid, echo, range_os=range_os)
+
+        @staticmethod
+        def backward(ctx, grad_image):
+            g = bpa_traj_gradient(ctx.pos, ctx.freqs, ctx.grid, ctx.echo, grad_image, range_os=ctx.range_os)
+            return g.to(ctx.offsets_device), None, None, None, None, None
+
+    return _BPAOffsets
+
+
+_BPA_OFFSETS = None
+
+
+def bpa_image_with_offsets(offsets, traj, freqs, grid, echo, range_os=16):
+    """Differentiable direct BPA image (complex64 CUDA tensor) of the positions traj +
+    offsets, offsets a float64 tensor [n_pos][3] (autofocus of uncertain tracks)."""
+    global _BPA_OFFSETS
+    if _BPA_OFFSETS is None:
+        _BPA_OFFSETS = _bpa_offsets_function()
+    return _BPA_OFFSETS.apply(offsets, traj, freqs, grid, echo, range_os)
 
 
 def bpa_form_image_noalloc(traj, freqs, grid, echo, out, stream=None, range_os=16):

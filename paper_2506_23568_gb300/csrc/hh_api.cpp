@@ -514,14 +514,13 @@ int hhffbp_plan_level_counts(const hh_plan* p, int64_t* evaluated, int32_t max_l
     return HH_OK;
 }
 
-int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
-                   const hh_config* cfg, const void* echo_c64, void* image_c64, void* cuda_stream) {
-    int st = hh::validate_inputs(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, false);
-    if (st != HH_OK) return st;
-    if (!echo_c64 || !image_c64) return HH_ERR_ARG;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-    // range constants and a gate covering every (voxel, position) distance
-    hh_plan tmp;
+}  // extern "C"
+
+namespace {
+// Range constants and a gate of stored bins covering every (voxel, position)
+// distance: the setup of direct BPA and of its gradient.
+void direct_bpa_setup(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                      const hh_config* cfg, hh_plan& tmp) {
     tmp.n_pos = n_pos;
     tmp.n_f = n_f;
     tmp.grid = *grid;
@@ -550,6 +549,19 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
         tmp.gate_n = tmp.n_fft;
         tmp.gate_wrap = true;
     }
+}
+}  // namespace
+
+extern "C" {
+
+int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                   const hh_config* cfg, const void* echo_c64, void* image_c64, void* cuda_stream) {
+    int st = hh::validate_inputs(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, false);
+    if (st != HH_OK) return st;
+    if (!echo_c64 || !image_c64) return HH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    hh_plan tmp;
+    direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
     const hh::KConst kc = hh::make_kconst(&tmp);
     std::vector<float> tw = hh::twiddle_table(tmp.n_fft);
     const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
@@ -589,6 +601,55 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
                           cuda_stream));
     HH_STEP(hh::launch_bpa(static_cast<const double*>(d_traj), n_pos, d_prof, kc, *grid, image, d_cnt, cuda_stream));
     if (host_img) HH_STEP(cudaMemcpyAsync(image_c64, image, 8 * (size_t)n_vox, cudaMemcpyDeviceToHost, s));
+    release();
+#undef HH_STEP
+    return HH_OK;
+}
+
+int bpa_traj_gradient(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f,
+                      const hh_grid* grid, const hh_config* cfg, const void* echo_c64, const void* grad_image_c64,
+                      double* grad_traj, void* cuda_stream) {
+    int st = hh::validate_inputs(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, false);
+    if (st != HH_OK) return st;
+    if (!echo_c64 || !grad_image_c64 || !grad_traj) return HH_ERR_ARG;
+    if (is_host_pointer(grad_image_c64) || is_host_pointer(grad_traj)) return HH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    hh_plan tmp;
+    direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
+    const hh::KConst kc = hh::make_kconst(&tmp);
+    std::vector<float> tw = hh::twiddle_table(tmp.n_fft);
+    const bool host_echo = is_host_pointer(echo_c64);
+    void *d_traj = nullptr, *d_prof = nullptr, *d_tw = nullptr, *d_cnt = nullptr, *d_echo = nullptr;
+    auto release = [&]() {
+        for (void* b : {d_traj, d_prof, d_tw, d_cnt, d_echo})
+            if (b) cudaFreeAsync(b, s);
+    };
+#define HH_STEP(call)                          \
+    do {                                       \
+        cudaError_t e_ = (cudaError_t)(call);  \
+        if (e_ != cudaSuccess) {               \
+            release();                         \
+            return fail_cuda(e_);              \
+        }                                      \
+    } while (0)
+    HH_STEP(cudaMallocAsync(&d_traj, sizeof(double) * 3 * n_pos, s));
+    HH_STEP(cudaMallocAsync(&d_prof, 16 * (size_t)n_pos * (size_t)tmp.gate_n, s));
+    HH_STEP(cudaMallocAsync(&d_tw, sizeof(float) * tw.size(), s));
+    HH_STEP(cudaMallocAsync(&d_cnt, sizeof(int64_t) * hh::CNT_N, s));
+    const void* echo = echo_c64;
+    if (host_echo) {
+        HH_STEP(cudaMallocAsync(&d_echo, 8 * (size_t)n_pos * n_f, s));
+        HH_STEP(cudaMemcpyAsync(d_echo, echo_c64, 8 * (size_t)n_pos * n_f, cudaMemcpyHostToDevice, s));
+        echo = d_echo;
+    }
+    HH_STEP(cudaMemcpyAsync(d_traj, traj_xyz, sizeof(double) * 3 * n_pos, cudaMemcpyHostToDevice, s));
+    HH_STEP(cudaMemcpyAsync(d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice, s));
+    HH_STEP(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * hh::CNT_N, s));
+    HH_STEP(cudaMemsetAsync(grad_traj, 0, sizeof(double) * 3 * (size_t)n_pos, s));
+    HH_STEP(hh::launch_rc(echo, nullptr, n_pos, n_f, tmp.n_fft, tmp.gate0, tmp.gate_n, d_tw, d_prof, nullptr,
+                          cuda_stream));
+    HH_STEP(hh::launch_bpa_grad(static_cast<const double*>(d_traj), n_pos, d_prof, kc, *grid, grad_image_c64,
+                                grad_traj, d_cnt, cuda_stream));
     release();
 #undef HH_STEP
     return HH_OK;

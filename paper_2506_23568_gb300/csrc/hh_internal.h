@@ -207,6 +207,8 @@ int launch_rc(const void* echo, const int64_t* d_perm, int64_t n_pos, int n_f, i
               int64_t gate_n, const void* d_twiddle, void* d_prof, void* d_prof2, void* stream);
 int launch_bpa(const double* d_traj, int64_t n_pos, const void* d_prof, const KConst& kc, const hh_grid& g,
                void* d_image, void* d_counters, void* stream);
+int launch_bpa_grad(const double* d_traj, int64_t n_pos, const void* d_prof, const KConst& kc, const hh_grid& g,
+                    const void* d_gimg, double* d_grad, void* d_counters, void* stream);
 int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);
 int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_tile_refs(const hh_plan* p, const KConst& kc, int level, void* stream);

@@ -180,7 +180,40 @@ def small(n_lines=16, n_per_line=16, n_f=32, nx=24, ny=20, nz=6, seed=1100):
                  centred_grid(nx, ny, nz, 2.5e-3, 2.5e-3, 1e-2, 0.17), None, seed + 1000)
 
 
-CONFIGS = {"tiny": tiny, "mid": mid, "large": large, "small": small}
+def diff():
+    """Differentiation scene: 8,192 positions (nominal track), 128 freqs, 32 points,
+    128x128x32 grid.  The echoes of this scene come from the true track, nominal +
+    diff_offsets() (smooth, 1 mm rms per axis): see diff_echo()."""
+    rng = np.random.default_rng(1003)
+    traj = random_walk_raster(rng, 64, 128, 0.25, 0.25, 0.5e-3, 5e-3, 5e-3)
+    n_s = 32
+    pos = np.column_stack([rng.uniform(-0.1, 0.1, n_s), rng.uniform(-0.1, 0.1, n_s),
+                           rng.uniform(0.22, 0.38, n_s)])
+    return Scene("diff", traj, freq_list(76e9, 81e9, 128), pos, np.ones(n_s, np.complex128),
+                 centred_grid(128, 128, 32, 2e-3, 2e-3, 6.25e-3, 0.2), None, 2003)
+
+
+def diff_offsets(n_pos, seed=3003, sigma_t=128.0, rms=1e-3):
+    """Smooth position offsets: white Gaussian noise per axis, filtered along the track by a
+    Gaussian of sigma_t samples, scaled to `rms` metres rms per axis."""
+    rng = np.random.default_rng(seed)
+    w = rng.normal(size=(n_pos, 3))
+    half = int(4 * sigma_t)
+    ker = np.exp(-0.5 * (np.arange(-half, half + 1) / sigma_t) ** 2)
+    out = np.column_stack([np.convolve(w[:, a], ker, mode="same") for a in range(3)])
+    out -= out.mean(axis=0)
+    return out * (rms / np.sqrt((out ** 2).mean(axis=0)))
+
+
+def diff_echo(scene, offsets, device="cpu"):
+    """complex64 echoes of the scene recorded along the true track traj + offsets."""
+    import torch
+
+    e = echoes(np.asarray(scene.traj) + offsets, scene.freqs, scene.scat_pos, scene.scat_amp, device=device)
+    return e.to(torch.complex64)
+
+
+CONFIGS = {"tiny": tiny, "mid": mid, "large": large, "small": small, "diff": diff}
 
 
 def echoes(traj, freqs, scat_pos, scat_amp, device="cpu", max_elems=1 << 25):

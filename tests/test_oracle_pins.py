@@ -360,3 +360,39 @@ def test_plant_mistake_in_interpolation_is_caught():
     bad, _ = oracle.Plan(s.traj, s.freqs, s.grid, leaf_size=16, eta=1.0, taps=2).hhffbpa(e)
     assert oracle.nrmse_db(good, bpa) < -35
     assert oracle.nrmse_db(bad, bpa) > -20
+
+
+# --------------------------------------------------------------------------- trajectory gradient
+def test_bpa_rc_traj_grad_matches_finite_differences():
+    """The oracle's position gradient of L = Re sum conj(g) f against central differences of
+    the oracle's own BPA-RC image (C code, an independent evaluation of the same sum)."""
+    s = synth.small()
+    e = synth.scene_echo(s).numpy()
+    rng = np.random.default_rng(7)
+    pts = s.grid.points(rng.choice(s.grid.n_vox, 40, replace=False))
+    g = rng.normal(size=40) + 1j * rng.normal(size=40)
+    G = oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, g)
+
+    def loss(traj):
+        return (np.conj(g) * oracle.bpa_rc(traj, s.freqs, e, pts)).real.sum()
+
+    h = 1e-9  # far below the range bin (1.87 mm): no lerp kink is crossed
+    for i, ax in [(0, 0), (5, 1), (17, 2), (100, 0), (200, 2), (255, 1)]:
+        tp, tm = s.traj.copy(), s.traj.copy()
+        tp[i, ax] += h
+        tm[i, ax] -= h
+        fd = (loss(tp) - loss(tm)) / (2 * h)
+        assert abs(fd - G[i, ax]) <= 1e-5 * abs(G[i, ax]), (i, ax, fd, G[i, ax])
+
+
+def test_bpa_rc_traj_grad_vanishes_for_zero_image_gradient_and_is_linear():
+    s = synth.small()
+    e = synth.scene_echo(s).numpy()
+    rng = np.random.default_rng(8)
+    pts = s.grid.points(rng.choice(s.grid.n_vox, 16, replace=False))
+    g1 = rng.normal(size=16) + 1j * rng.normal(size=16)
+    g2 = rng.normal(size=16) + 1j * rng.normal(size=16)
+    assert np.all(oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, np.zeros(16)) == 0)
+    a = oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, g1 + 2 * g2)
+    b = oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, g1) + 2 * oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, g2)
+    np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-9 * np.abs(a).max())

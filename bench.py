@@ -311,6 +311,26 @@ def run_gpu(args):
     units = {"fp32": dom["flop"], "mufu": dom["mufu"], "hbm": dom["bytes"]}[kind]
     d_ach, d_peak, d_unit, d_bound, d_frac = roofline_of(kind, dom["ms"], units, peaks, clk_mhz)
 
+    # position gradient of direct BPA on the differentiation scene (8,192 positions, 128 freqs,
+    # 128x128x32 grid, echoes from a track with smooth 1 mm offsets): CUDA events around the call
+    ds = synth.diff()
+    d_echo = synth.diff_echo(ds, synth.diff_offsets(len(ds.traj)), device="cuda")
+    d_g = torch.randn(ds.grid.shape, dtype=torch.complex64, device="cuda",
+                      generator=torch.Generator(device="cuda").manual_seed(17))
+    d_out = torch.empty((len(ds.traj), 3), dtype=torch.float64, device="cuda")
+    d_times = []
+    for i in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hh.bpa_traj_gradient(ds.traj, ds.freqs, ds.grid, d_echo, d_g, out=d_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            d_times.append(e0.elapsed_time(e1))
+    d_ms = statistics.median(d_times)
+    d_upd = ds.grid.n_vox * len(ds.traj)
+    g_ach, g_peak, g_unit, g_bound, g_frac = roofline_of("mufu", d_ms, d_upd * BPA_MUFU, peaks, clk_mhz)
+
     # e2e through the C ABI with pinned host buffers (H2D echo, D2H image inside the timed region)
     h_echo = echo.cpu().pin_memory()
     h_img = torch.empty(grid.shape, dtype=torch.complex64).pin_memory()
@@ -377,6 +397,11 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(h_echo.numel() * 8 + s.traj.size * 8 + s.freqs.size * 8),
                 "d2h_bytes_per_step": int(h_img.numel() * 8)},
         "gpu_launches": n_launch * args.steps,
+        "position_gradient": {"workload": "diff: 8,192 positions, 128 freqs, 32 points, 128x128x32 grid, "
+                                          "smooth 1 mm track offsets", "ms": d_ms,
+                              "updates": d_upd, "achieved": g_ach, "peak": g_peak, "unit": g_unit,
+                              "bound": g_bound, "frac": g_frac,
+                              "note": "bpa_traj_gradient incl. range compression; outside the timed steps"},
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:

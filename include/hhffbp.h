@@ -89,6 +89,16 @@ typedef struct hh_plan hh_plan;
 int hhffbp_default_config(hh_config* cfg);
 
 /*
+ * hhffbp_interp_weights -- the interpolation weights the merge kernels use, evaluated on
+ * the host exactly as the kernels do (FP32 polynomials of x = 2 tau - 1, degree 8, fitted
+ * to the least-squares fractional-delay weights for lattice density eta; Sec. IV-A leaves
+ * the interpolator open).  tau: host float64 [n] in [0, 1); out: host float64 [n][taps],
+ * weight q for the sample at offset q - (taps/2 - 1) from floor(index).  taps: 4 or 6.
+ * Errors: HH_ERR_ARG.
+ */
+int hhffbp_interp_weights(int32_t taps, double eta, const double* tau, int64_t n, double* out);
+
+/*
  * hhffbp_plan -- build the subarray tree and the compressed sampling grids
  * (Sec. IV-A: 2^(M-1) level-1 subarrays; uniform grids in (u, v, n) of
  * Eq. eq_uvw_xyz per subarray), allocate the device workspace and upload the

@@ -35,7 +35,7 @@ HH_ERR_SCRATCH_LIMIT = 9
 HH_FLAG_HOST_ONLY = 1
 
 # every symbol declared in include/hhffbp.h
-SYMBOLS = ["hhffbp_default_config", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
+SYMBOLS = ["hhffbp_default_config", "hhffbp_interp_weights", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
            "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
            "hhffbp_plan_stage_times", "hhffbp_plan_preimages",
            "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "hhffbp_adjoint", "hh_status_string",
@@ -93,6 +93,7 @@ def lib(build_if_needed=True):
 def _declare(L):
     vp, dp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
     L.hhffbp_default_config.argtypes = [ctypes.POINTER(hh_config)]
+    L.hhffbp_interp_weights.argtypes = [ctypes.c_int32, ctypes.c_double, dp, ctypes.c_int64, dp]
     L.hhffbp_plan.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
                               ctypes.POINTER(hh_config), vp, ctypes.POINTER(vp)]
     L.hhffbp_plan_destroy.argtypes = [vp]
@@ -118,6 +119,16 @@ def _declare(L):
         f = getattr(L, name)
         if name != "hh_status_string":
             f.restype = ctypes.c_int
+
+
+def interp_weights(taps, eta, tau):
+    """The merge kernels' interpolation weights at fractional positions tau (float64 [n][taps])."""
+    t = _f64(tau).ravel()
+    out = np.zeros((len(t), int(taps)))
+    _check(lib().hhffbp_interp_weights(int(taps), float(eta), t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       len(t), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "interp_weights")
+    return out
 
 
 def status_string(status):

@@ -230,6 +230,22 @@ int hhffbp_default_config(hh_config* cfg) {
     return HH_OK;
 }
 
+int hhffbp_interp_weights(int32_t taps, double eta, const double* tau, int64_t n, double* out) {
+    if ((taps != 4 && taps != 6) || !(eta >= 1.0) || n < 0 || (n > 0 && (!tau || !out))) return HH_ERR_ARG;
+    const hh::WPoly wp = hh::weight_poly(taps, eta);
+    for (int64_t i = 0; i < n; ++i) {  // the kernels' evaluation (footprint()), in FP32 with fused multiply-adds
+        const float x = std::fmaf(2.f, (float)tau[i], -1.f), x2 = x * x;
+        for (int q = 0; q < taps / 2; ++q) {
+            float e = wp.e[q][4], o = wp.o[q][3];
+            for (int j = 3; j >= 0; --j) e = std::fmaf(e, x2, wp.e[q][j]);
+            for (int j = 2; j >= 0; --j) o = std::fmaf(o, x2, wp.o[q][j]);
+            out[i * taps + q] = std::fmaf(x, o, e);
+            out[i * taps + taps - 1 - q] = std::fmaf(-x, o, e);
+        }
+    }
+    return HH_OK;
+}
+
 int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
                 const hh_config* cfg, void* cuda_stream, hh_plan** out) {
     if (!out) return HH_ERR_ARG;

@@ -119,3 +119,23 @@ def test_host_only_plan_refuses_imaging():
     assert st == hh.HH_ERR_HOST_ONLY
     assert L.hhffbp_form_image(None, None, None, None) == hh.HH_ERR_ARG
     assert L.hhffbp_adjoint(p._h, None, None, None) == hh.HH_ERR_UNIMPLEMENTED
+
+
+@pytest.mark.parametrize("taps,eta", [(4, 2.0), (6, 1.6), (6, 1.75), (6, 2.0)])
+def test_kernel_interp_weights_match_oracle_least_squares(taps, eta):
+    """The merge kernels' interpolation weights (FP32 polynomials, evaluated as the kernels do)
+    against the oracle's least-squares weights: within the FP32 rounding level everywhere on
+    [0, 1), exact partition of unity to that level, and the identity at tau = 0."""
+    tau = np.linspace(0.0, 1.0, 2001, endpoint=False)
+    got = hh.interp_weights(taps, eta, tau)
+    ref = oracle.ls_weights(taps, eta, tau)
+    assert np.abs(got - ref).max() < 5e-7
+    o = np.arange(-(taps // 2 - 1), taps // 2 + 1)
+    np.testing.assert_allclose(got[0], (o == 0).astype(float), atol=5e-7)
+
+
+def test_kernel_interp_weights_reject_bad_arguments():
+    with pytest.raises(hh.LibraryError):
+        hh.interp_weights(5, 2.0, [0.5])
+    with pytest.raises(hh.LibraryError):
+        hh.interp_weights(6, 0.5, [0.5])

@@ -43,15 +43,16 @@ PLAN_CFG = {"large": dict(leaf_size=256, eta=1.6), "mid": dict(leaf_size=256, et
             "tiny": dict(leaf_size=32)}
 
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
-# benchmark command on the large workload (profiles/launches_large_bench.md); valid for the
-# kernels and plan they were taken with, reported as null otherwise.
+# benchmark command on the large workload (the launch-list summary under profiles/); valid
+# for the kernels and plan they were taken with, reported as null otherwise.
 TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.6, 6): 823.7e6,
            ("large", "merge", 1, 256, 1.6, 6): 1498.5e6,
            ("large", "merge", 2, 256, 1.6, 6): 923.7e6,
            ("large", "merge", 3, 256, 1.6, 6): 915.6e6,
            ("large", "final", 4, 256, 1.6, 6): 1797.1e6}
 
-# Algorithmic work per unit ("Measurement"):
+# Algorithmic work per unit: a BPA-type update (one position at one point) takes one
+# rsqrt and one sincos (3 MUFU results) and about 25 FP32 operations
 BPA_FLOP, BPA_MUFU = 25.0, 3.0            # per (voxel, position) update
 MUFU_PER_SM_CLK = 16.0                    # SFU results per SM per clock (sm_100-class)
 FP32_PER_SM_CLK = 256.0                   # 128 FMA lanes x 2 FLOP

@@ -38,7 +38,7 @@ WORKLOADS = {
 }
 # Plan per workload: leaf subarrays of 256 positions, 4-way merges, 6-tap LS interpolation on
 # lattices at 1.6x the measured spectral extent (-36.9 dB NRMSE vs direct BPA on large; 1.75x
-# gives -42.1 dB at 16 % more time, 1.5x -33.1 dB at 10 % less).
+# gives -42.1 dB at 16 % more kernel time, 1.55x -35.1 dB at 6 % less).
 PLAN_CFG = {"large": dict(leaf_size=256, eta=1.6), "mid": dict(leaf_size=256, eta=1.6),
             "tiny": dict(leaf_size=32)}
 

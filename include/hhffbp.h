@@ -218,6 +218,20 @@ int bpa_traj_gradient(const double* traj_xyz, int64_t n_pos, const double* freqs
                       double* grad_traj, void* cuda_stream);
 
 /*
+ * bpa_adjoint -- adjoint of bpa_form_image (reprojection: image -> echoes), the linear
+ * map's conjugate transpose:
+ *   s_i[n] = sum_m exp(-j theta_n m) sum_p x(p) exp(-j 2 k_c R_i) w_m(R_i / dR),
+ * theta_n = 2 pi (n - (N_f - 1)/2) / N_fft, w_m the linear-interpolation weights of bin m
+ * (Eqs. eq2_rangecompression, eq2_bpatimedomain transposed; the paper forms images
+ * only).  image_c64: device complex64 [nz][ny][nx]; echo_c64: device complex64
+ * [n_pos][n_f], overwritten.  traj_xyz, freqs_hz: host float64.  Only cfg->range_os is
+ * used.  Workspace is allocated and freed stream-ordered.  Asynchronous on cuda_stream.
+ * Errors: HH_ERR_ARG (null or host buffers), HH_ERR_FREQ_NONUNIFORM, HH_ERR_OOM, HH_ERR_CUDA.
+ */
+int bpa_adjoint(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                const hh_config* cfg, const void* image_c64, void* echo_c64, void* cuda_stream);
+
+/*
  * bpa_form_image_noalloc -- bpa_form_image for callers that cannot allocate
  * memory during the call.  The paper has no counterpart: it is an interface
  * variant of the same computation (Eqs. eq2_rangecompression and

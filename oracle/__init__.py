@@ -171,6 +171,27 @@ def bpa_rc_traj_grad(traj, freqs, echo, pts, g, os_r=16):
     return ((a / R)[:, :, None] * d).sum(axis=1)
 
 
+def bpa_rc_adjoint(traj, freqs, x, pts, os_r=16):
+    """Adjoint of the BPA-RC image at the points pts (Eqs. eq2_rangecompression,
+    eq2_bpatimedomain): s[i, n] = sum_p x_p exp(-j 2 k_c R) [(1 - t) e^{-j th_n m0} + t e^{-j th_n (m0+1)}],
+    th_n = 2 pi (n - (N_f - 1)/2) / N_fft, m0 = floor(R / dR), t = R / dR - m0: the conjugate
+    transpose of f = A s written out, in FP64.  Returns complex128 [n_pos][n_f]."""
+    t, p = _f64(traj), _f64(pts)
+    x = np.asarray(x, np.complex128).ravel()
+    n_f = len(np.asarray(freqs))
+    n_fft, dR, kc, _ = rc_params(freqs, os_r)
+    d = t[:, None, :] - p[None, :, :]
+    R = np.sqrt((d * d).sum(-1))
+    mu = R / dR
+    m0 = np.floor(mu)
+    frac = mu - m0
+    th = 2 * np.pi * (np.arange(n_f) - (n_f - 1) / 2) / n_fft
+    c = x[None, :] * np.exp(-2j * kc * R)  # [n_pos, n_pts]
+    e0 = np.exp(-1j * th[None, None, :] * m0[:, :, None])
+    e1 = e0 * np.exp(-1j * th)[None, None, :]
+    return ((c * (1 - frac))[:, :, None] * e0 + (c * frac)[:, :, None] * e1).sum(axis=1)
+
+
 def keypoints(rect, zbar, kmin, kmax, p):
     """(k[7][3], Ts[3][3]) at point p for subarray rect = (a, b, e, g)."""
     r, pp = _f64(rect), _f64(p)

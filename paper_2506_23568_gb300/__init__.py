@@ -19,7 +19,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Grid", "Config", "Plan", "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient",
+__all__ = ["Grid", "Config", "Plan", "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "bpa_adjoint",
            "bpa_image_with_offsets", "lib", "LibraryError", "status_string", "SYMBOLS"]
 
 HH_OK = 0
@@ -38,7 +38,8 @@ HH_FLAG_HOST_ONLY = 1
 SYMBOLS = ["hhffbp_default_config", "hhffbp_interp_weights", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
            "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
            "hhffbp_plan_stage_times", "hhffbp_plan_preimages",
-           "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "hhffbp_adjoint", "hh_status_string",
+           "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "bpa_adjoint", "hhffbp_adjoint",
+           "hh_status_string",
            "hh_last_cuda_error",
            "hh_release_cached_memory"]
 STAGE_NAMES = {0: "range_compression", 1: "need_final", 2: "need_level", 3: "leaf_subimages", 4: "merge",
@@ -110,6 +111,8 @@ def _declare(L):
                                  ctypes.POINTER(hh_config), vp, vp, vp]
     L.bpa_traj_gradient.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
                                     ctypes.POINTER(hh_config), vp, vp, vp, vp]
+    L.bpa_adjoint.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
+                              ctypes.POINTER(hh_config), vp, vp, vp]
     L.hhffbp_adjoint.argtypes = [vp, vp, vp, vp]
     L.hh_status_string.argtypes = [ctypes.c_int]
     L.hh_status_string.restype = ctypes.c_char_p
@@ -343,6 +346,26 @@ def bpa_traj_gradient(traj, freqs, grid, echo, grad_image, out=None, stream=None
                                    ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(gi), _buffer_ptr(out),
                                    _stream_ptr(stream)),
            "bpa_traj_gradient")
+    return out
+
+
+def bpa_adjoint(traj, freqs, grid, image, out=None, stream=None, range_os=16):
+    """Adjoint of bpa_form_image (reprojection): complex64 [n_pos][n_f] echoes from a complex64
+    CUDA image [nz][ny][nx]."""
+    import torch
+
+    t, f = _f64(traj), _f64(freqs)
+    g = Grid.from_any(grid)
+    cfg = Config(range_os=range_os)
+    x = image.contiguous()
+    if x.dtype != torch.complex64:
+        x = x.to(torch.complex64)
+    if out is None:
+        out = torch.empty((len(t), len(f)), dtype=torch.complex64, device=x.device)
+    _check(lib().bpa_adjoint(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
+                             f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
+                             ctypes.byref(cfg), _buffer_ptr(x), _buffer_ptr(out), _stream_ptr(stream)),
+           "bpa_adjoint")
     return out
 
 

@@ -671,6 +671,46 @@ int bpa_traj_gradient(const double* traj_xyz, int64_t n_pos, const double* freqs
     return HH_OK;
 }
 
+int bpa_adjoint(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
+                const hh_config* cfg, const void* image_c64, void* echo_c64, void* cuda_stream) {
+    int st = hh::validate_inputs(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, false);
+    if (st != HH_OK) return st;
+    if (!image_c64 || !echo_c64) return HH_ERR_ARG;
+    if (is_host_pointer(image_c64) || is_host_pointer(echo_c64)) return HH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    hh_plan tmp;
+    direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
+    const hh::KConst kc = hh::make_kconst(&tmp);
+    std::vector<float> tw = hh::twiddle_table(tmp.n_fft);
+    void *d_traj = nullptr, *d_bins = nullptr, *d_tw = nullptr, *d_cnt = nullptr;
+    auto release = [&]() {
+        for (void* b : {d_traj, d_bins, d_tw, d_cnt})
+            if (b) cudaFreeAsync(b, s);
+    };
+#define HH_STEP(call)                          \
+    do {                                       \
+        cudaError_t e_ = (cudaError_t)(call);  \
+        if (e_ != cudaSuccess) {               \
+            release();                         \
+            return fail_cuda(e_);              \
+        }                                      \
+    } while (0)
+    const size_t bins_bytes = 8 * (size_t)n_pos * (size_t)(tmp.gate_n + 1);
+    HH_STEP(cudaMallocAsync(&d_traj, sizeof(double) * 3 * n_pos, s));
+    HH_STEP(cudaMallocAsync(&d_bins, bins_bytes, s));
+    HH_STEP(cudaMallocAsync(&d_tw, sizeof(float) * tw.size(), s));
+    HH_STEP(cudaMallocAsync(&d_cnt, sizeof(int64_t) * hh::CNT_N, s));
+    HH_STEP(cudaMemcpyAsync(d_traj, traj_xyz, sizeof(double) * 3 * n_pos, cudaMemcpyHostToDevice, s));
+    HH_STEP(cudaMemcpyAsync(d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice, s));
+    HH_STEP(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * hh::CNT_N, s));
+    HH_STEP(cudaMemsetAsync(d_bins, 0, bins_bytes, s));
+    HH_STEP(hh::launch_bpa_adjoint(static_cast<const double*>(d_traj), n_pos, n_f, kc, *grid, image_c64, d_bins, d_tw,
+                                   tmp.n_fft, tmp.gate0, tmp.gate_n, echo_c64, d_cnt, cuda_stream));
+    release();
+#undef HH_STEP
+    return HH_OK;
+}
+
 int hhffbp_plan_preimages(const hh_plan* p, int64_t node, const double* targets, int64_t n, double* out,
                           void* cuda_stream) {
     if (!p || !targets || !out || n < 0) return HH_ERR_ARG;

@@ -209,6 +209,9 @@ int launch_bpa(const double* d_traj, int64_t n_pos, const void* d_prof, const KC
                void* d_image, void* d_counters, void* stream);
 int launch_bpa_grad(const double* d_traj, int64_t n_pos, const void* d_prof, const KConst& kc, const hh_grid& g,
                     const void* d_gimg, double* d_grad, void* d_counters, void* stream);
+int launch_bpa_adjoint(const double* d_traj, int64_t n_pos, int n_f, const KConst& kc, const hh_grid& g,
+                       const void* d_img, void* d_bins, const void* d_twiddle, int n_fft, int64_t gate0, int64_t gate_n,
+                       void* d_echo, void* d_counters, void* stream);
 int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);
 int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_tile_refs(const hh_plan* p, const KConst& kc, int level, void* stream);

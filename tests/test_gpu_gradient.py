@@ -1,5 +1,6 @@
-"""GPU position gradient of direct BPA (bpa_traj_gradient) against the FP64 oracle, and the
-differentiable image (bpa_image_with_offsets) against finite differences of a loss.
+"""GPU position gradient of direct BPA (bpa_traj_gradient) and its adjoint (bpa_adjoint)
+against the FP64 oracle, and the differentiable image (bpa_image_with_offsets) against
+finite differences of a loss.
 
 The kernel differentiates the BPA sum term by term; the oracle does the same in FP64
 (pinned by finite differences of its own BPA-RC on the CPU).  Tolerance: relative L2
@@ -72,3 +73,33 @@ def test_autofocus_loss_gradient_matches_finite_differences(hh):
     fd = (lp - lm) / (2 * h)
     an = float((grad * v).sum())
     assert abs(fd - an) <= 2e-2 * abs(an), (fd, an)
+
+
+@pytest.mark.parametrize("name", ["small", "diff"])
+def test_bpa_adjoint_matches_oracle(hh, name):
+    s = synth.CONFIGS[name]()
+    g = s.grid
+    rng = np.random.default_rng(12)
+    idx = rng.choice(g.n_vox, 96, replace=False)
+    xv = (rng.normal(size=96) + 1j * rng.normal(size=96)).astype(np.complex64)
+    x = torch.zeros(g.n_vox, dtype=torch.complex64, device="cuda")
+    x[torch.as_tensor(idx, device="cuda")] = torch.as_tensor(xv, device="cuda")
+    got = hh.bpa_adjoint(s.traj, s.freqs, g, x.reshape(g.shape)).cpu().numpy()
+    ref = oracle.bpa_rc_adjoint(s.traj, s.freqs, xv.astype(np.complex128), g.points(idx))
+    assert got.shape == (len(s.traj), len(s.freqs))
+    assert oracle.rel_l2(got.astype(np.complex128).ravel(), ref.ravel()) < REL_TOL
+
+
+def test_bpa_adjoint_dot_product_with_forward(hh):
+    """<x, A s> = <A^H x, s> with the GPU's forward and adjoint on a full grid (FP32)."""
+    s = synth.small()
+    rng = np.random.default_rng(13)
+    e = torch.as_tensor((rng.normal(size=(len(s.traj), len(s.freqs)))
+                         + 1j * rng.normal(size=(len(s.traj), len(s.freqs)))).astype(np.complex64), device="cuda")
+    x = torch.as_tensor((rng.normal(size=s.grid.shape) + 1j * rng.normal(size=s.grid.shape)).astype(np.complex64),
+                        device="cuda")
+    fwd = hh.bpa_form_image(s.traj, s.freqs, s.grid, e)
+    adj = hh.bpa_adjoint(s.traj, s.freqs, s.grid, x)
+    lhs = torch.vdot(x.reshape(-1).to(torch.complex128), fwd.reshape(-1).to(torch.complex128)).item()
+    rhs = torch.vdot(adj.reshape(-1).to(torch.complex128), e.reshape(-1).to(torch.complex128)).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)

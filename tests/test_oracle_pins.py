@@ -396,3 +396,15 @@ def test_bpa_rc_traj_grad_vanishes_for_zero_image_gradient_and_is_linear():
     a = oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, g1 + 2 * g2)
     b = oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, g1) + 2 * oracle.bpa_rc_traj_grad(s.traj, s.freqs, e, pts, g2)
     np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-9 * np.abs(a).max())
+
+
+def test_bpa_rc_adjoint_dot_product_identity():
+    """<x, A s> = <A^H x, s> for the oracle's BPA-RC (C) and its adjoint written out (numpy)."""
+    s = synth.small()
+    rng = np.random.default_rng(3)
+    e = rng.normal(size=(len(s.traj), len(s.freqs))) + 1j * rng.normal(size=(len(s.traj), len(s.freqs)))
+    pts = s.grid.points(rng.choice(s.grid.n_vox, 50, replace=False))
+    x = rng.normal(size=50) + 1j * rng.normal(size=50)
+    lhs = np.vdot(x, oracle.bpa_rc(s.traj, s.freqs, e, pts))
+    rhs = np.vdot(oracle.bpa_rc_adjoint(s.traj, s.freqs, x, pts), e)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)

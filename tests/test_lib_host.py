@@ -139,3 +139,29 @@ def test_kernel_interp_weights_reject_bad_arguments():
         hh.interp_weights(5, 2.0, [0.5])
     with pytest.raises(hh.LibraryError):
         hh.interp_weights(6, 0.5, [0.5])
+
+
+def test_gradient_and_adjoint_refuse_null_buffers_without_cuda():
+    """Argument errors of the direct-BPA gradient and adjoint entry points are returned before
+    any CUDA call (no device needed): null echo/image/gradient buffers and bad inputs."""
+    L = hh.lib()
+    s = synth.small()
+    t = np.ascontiguousarray(s.traj, np.float64)
+    f = np.ascontiguousarray(s.freqs, np.float64)
+    g = hh.Grid.from_any(s.grid)
+    cfg = hh.Config(range_os=16)
+    dp = ctypes.POINTER(ctypes.c_double)
+    tp, fp = t.ctypes.data_as(dp), f.ctypes.data_as(dp)
+    dummy = ctypes.c_void_p(1)
+    assert L.bpa_traj_gradient(tp, len(t), fp, len(f), ctypes.byref(g), ctypes.byref(cfg), None, dummy, dummy,
+                               None) == hh.HH_ERR_ARG
+    assert L.bpa_traj_gradient(tp, len(t), fp, len(f), ctypes.byref(g), ctypes.byref(cfg), dummy, None, dummy,
+                               None) == hh.HH_ERR_ARG
+    assert L.bpa_traj_gradient(tp, len(t), fp, len(f), ctypes.byref(g), ctypes.byref(cfg), dummy, dummy, None,
+                               None) == hh.HH_ERR_ARG
+    assert L.bpa_adjoint(tp, len(t), fp, len(f), ctypes.byref(g), ctypes.byref(cfg), None, dummy,
+                         None) == hh.HH_ERR_ARG
+    assert L.bpa_adjoint(tp, len(t), fp, len(f), ctypes.byref(g), ctypes.byref(cfg), dummy, None,
+                         None) == hh.HH_ERR_ARG
+    assert L.bpa_adjoint(tp, 0, fp, len(f), ctypes.byref(g), ctypes.byref(cfg), dummy, dummy,
+                         None) == hh.HH_ERR_ARG

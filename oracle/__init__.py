@@ -83,6 +83,8 @@ def _declare(L):
     L.hho_plan_export.argtypes = [ctypes.c_void_p, _ip, _ip, _dp, _dp]
     L.hho_hhffbpa.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _dp, _i64, _dp, _ip]
     L.hho_hhffbpa.restype = ctypes.c_int
+    L.hho_hhffbpa_adjoint.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _dp, _i64, _dp]
+    L.hho_hhffbpa_adjoint.restype = ctypes.c_int
     L.hho_num_threads.restype = ctypes.c_int
 
 
@@ -174,8 +176,9 @@ def bpa_rc_traj_grad(traj, freqs, echo, pts, g, os_r=16):
 def bpa_rc_adjoint(traj, freqs, x, pts, os_r=16):
     """Adjoint of the BPA-RC image at the points pts (Eqs. eq2_rangecompression,
     eq2_bpatimedomain): s[i, n] = sum_p x_p exp(-j 2 k_c R) [(1 - t) e^{-j th_n m0} + t e^{-j th_n (m0+1)}],
-    th_n = 2 pi (n - (N_f - 1)/2) / N_fft, m0 = floor(R / dR), t = R / dR - m0: the conjugate
-    transpose of f = A s written out, in FP64.  Returns complex128 [n_pos][n_f]."""
+    th_n = 2 pi (n - (N_f - 1)/2) / N_fft, m0 = floor(R / dR) (bins mod N_fft, as the profiles),
+    t = R / dR - m0: the conjugate transpose of f = A s written out, in FP64.  Returns
+    complex128 [n_pos][n_f]."""
     t, p = _f64(traj), _f64(pts)
     x = np.asarray(x, np.complex128).ravel()
     n_f = len(np.asarray(freqs))
@@ -187,8 +190,9 @@ def bpa_rc_adjoint(traj, freqs, x, pts, os_r=16):
     frac = mu - m0
     th = 2 * np.pi * (np.arange(n_f) - (n_f - 1) / 2) / n_fft
     c = x[None, :] * np.exp(-2j * kc * R)  # [n_pos, n_pts]
-    e0 = np.exp(-1j * th[None, None, :] * m0[:, :, None])
-    e1 = e0 * np.exp(-1j * th)[None, None, :]
+    # bins taken mod N_fft, as the range profiles are (they are periodic in m up to that sign)
+    e0 = np.exp(-1j * th[None, None, :] * np.mod(m0, n_fft)[:, :, None])
+    e1 = np.exp(-1j * th[None, None, :] * np.mod(m0 + 1, n_fft)[:, :, None])
     return ((c * (1 - frac))[:, :, None] * e0 + (c * frac)[:, :, None] * e1).sum(axis=1)
 
 
@@ -281,6 +285,21 @@ class Plan:
                     eta=nd[:, 7:10], node_zbar=nd[:, 10],
                     zbar=sc[0], kmin=sc[1], kmax=sc[2], zh_floor=sc[3], zh_mid=sc[4], min_ext=sc[5],
                     **inf)
+
+    def hhffbpa_adjoint(self, x, pts=None):
+        """Adjoint of hhffbpa (image values x at the points -> echoes, complex128 [n_pos][n_f]):
+        the forward map's conjugate transpose, taken step by step (final, merges, leaves, range
+        compression); the forward's interpolation/fallback choices depend on geometry alone."""
+        if pts is None:
+            pts = self.grid.points()
+        p = _f64(pts)
+        xr = _ri(np.asarray(x, np.complex128).ravel())
+        n_pos, n_f = len(self.traj), len(self.freqs)
+        out = np.zeros(2 * n_pos * n_f)
+        rc = lib().hho_hhffbpa_adjoint(self._h, _ptr(self.freqs), n_f, _ptr(xr), _ptr(p), len(p), _ptr(out))
+        if rc != 0:
+            raise RuntimeError(f"oracle hhffbpa adjoint failed: {rc}")
+        return _cplx(out, (n_pos, n_f))
 
     def hhffbpa(self, echo, pts=None):
         """HHFFBPA values at the given points (default: all voxels).  Returns (values, stats)."""

@@ -1215,6 +1215,240 @@ int hho_hhffbpa(const hho_plan* pl, const double* freqs, int n_f, const double* 
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the HHFFBPA map (echo -> image values at the points), the      */
+/* conjugate transpose of hho_hhffbpa taken step by step in reverse order:    */
+/*   final:   x_q -> each root child c: w e^{-j phi_c} x_q into c's footprint */
+/*            samples, or (fallback) the BPA-RC adjoint over c's members;     */
+/*   merges:  y = e^{+j Phi_P(p)} adj_P[q] -> the same child step at p;       */
+/*   leaves:  y = e^{+j Phi_L(p)} adj_L[q] -> BPA-RC adjoint over L's members */
+/*            at p: bins m0, m0+1 of each member get (1-t, t) e^{-j 2 k_c R} y;*/
+/*   range compression: s[i,n] = sum_m e^{-j theta_n (m mod N)} B_i[m].       */
+/* The interpolation/fallback choice depends on geometry alone (footprint    */
+/* inside the lattice, every footprint sample feasible), so the forward map  */
+/* is linear in the echo and this is its exact adjoint.                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    i64 n_pos, m_lo;
+    int n_bins, n_f, n_fft;
+    double dR, kc;
+    double* win;   /* [n_pos][n_bins][2]: adjoint of the profile window's bins */
+    double* extra; /* [n_pos][n_f][2]: bins outside the window, transformed at once */
+} adj_prof;
+
+static void adj_add_bin(adj_prof* A, i64 i, i64 m, double vr, double vi) {
+    i64 j = m - A->m_lo;
+    if (j >= 0 && j < A->n_bins) {
+        double* w = A->win + 2 * (i * A->n_bins + j);
+#pragma omp atomic
+        w[0] += vr;
+#pragma omp atomic
+        w[1] += vi;
+        return;
+    }
+    /* the adjoint of dft_bin for this one bin: conj(e^{+j pi (2n - N_f + 1) (m mod N) / N}) */
+    i64 mm = ((m % A->n_fft) + A->n_fft) % A->n_fft, period = 2 * (i64)A->n_fft;
+    for (int n = 0; n < A->n_f; ++n) {
+        i64 q = ((i64)(2 * n - A->n_f + 1) * mm) % period;
+        if (q < 0) q += period;
+        double ang = HHO_PI * (double)q / (double)A->n_fft;
+        double c = cos(ang), sn = -sin(ang);
+        double* e = A->extra + 2 * (i * A->n_f + n);
+#pragma omp atomic
+        e[0] += vr * c - vi * sn;
+#pragma omp atomic
+        e[1] += vr * sn + vi * c;
+    }
+}
+
+/* adjoint of bpa_rc_point: value y at point p over the members perm[b..e) */
+static void bpa_rc_point_adj(adj_prof* A, const double* traj, const i64* perm, i64 b, i64 e, const double p[3],
+                             const double y[2]) {
+    for (i64 jj = b; jj < e; ++jj) {
+        i64 i = perm ? perm[jj] : jj;
+        double dx = p[0] - traj[3 * i], dy = p[1] - traj[3 * i + 1], dz = p[2] - traj[3 * i + 2];
+        double R = sqrt(dx * dx + dy * dy + dz * dz);
+        double mu = R / A->dR;
+        double fl = floor(mu);
+        double t = mu - fl;
+        i64 m0 = (i64)fl;
+        double ph = 2.0 * A->kc * R;
+        double cr = cos(ph), ci = -sin(ph);
+        double vr = y[0] * cr - y[1] * ci, vi = y[0] * ci + y[1] * cr; /* e^{-j ph} y */
+        adj_add_bin(A, i, m0, (1.0 - t) * vr, (1.0 - t) * vi);
+        adj_add_bin(A, i, m0 + 1, t * vr, t * vi);
+    }
+}
+
+typedef struct {
+    uint8_t* need;
+    uint8_t* feas;  /* needed and feasible (preimage found) */
+    double* pre;    /* [N][4]: preimage x, y, z and Phi of the node there */
+    double* adj;    /* [N][2]: adjoint values of the samples */
+} adj_node;
+
+/* adjoint of child_contrib: value y of f_c at point p */
+static void child_contrib_adj(const hho_plan* pl, adj_prof* A, const hho_node* c, adj_node* cd, const double p[3],
+                              const double y[2]) {
+    footprint F;
+    make_footprint(pl, c, p, &F);
+    int T = pl->taps, ok = F.inside;
+    for (int a = 0; ok && a < T; ++a)
+        for (int b = 0; ok && b < T; ++b)
+            for (int q = 0; ok && q < T; ++q)
+                if (!cd->feas[lat_index(c, F.base[0] + a, F.base[1] + b, F.base[2] + q)]) ok = 0;
+    if (!ok) {
+        bpa_rc_point_adj(A, pl->traj, pl->perm, c->begin, c->end, p, y);
+        return;
+    }
+    double cr = cos(F.phi), ci = -sin(F.phi);
+    double vr = y[0] * cr - y[1] * ci, vi = y[0] * ci + y[1] * cr; /* e^{-j phi_c} y */
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            double wab = F.w[0][a] * F.w[1][b];
+            for (int q = 0; q < T; ++q) {
+                double ww = wab * F.w[2][q];
+                double* o = cd->adj + 2 * lat_index(c, F.base[0] + a, F.base[1] + b, F.base[2] + q);
+#pragma omp atomic
+                o[0] += ww * vr;
+#pragma omp atomic
+                o[1] += ww * vi;
+            }
+        }
+}
+
+int hho_hhffbpa_adjoint(const hho_plan* pl, const double* freqs, int n_f, const double* x_ri, const double* pts,
+                        i64 n_pts, double* echo_ri) {
+    int nl = pl->n_levels;
+    const hho_node* root = &pl->nodes[pl->level_start[nl - 1]];
+    double lo, hi;
+    range_bounds(pl->traj, pl->n_pos, pts, n_pts, &lo, &hi);
+    hho_prof P; /* the forward's profile window; only its bin range is used here */
+    prof_init(&P, NULL, 0, freqs, n_f, pl->os_r, lo - 0.3, hi + 0.3);
+    adj_prof A;
+    A.n_pos = pl->n_pos;
+    A.m_lo = P.m_lo;
+    A.n_bins = P.n_bins;
+    A.n_f = n_f;
+    A.n_fft = P.n_fft;
+    A.dR = P.dR;
+    A.kc = P.kc;
+    A.win = (double*)calloc((size_t)2 * pl->n_pos * P.n_bins, sizeof(double));
+    A.extra = (double*)calloc((size_t)2 * pl->n_pos * n_f, sizeof(double));
+    prof_free(&P);
+
+    if (nl == 1) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (i64 q = 0; q < n_pts; ++q) bpa_rc_point_adj(&A, pl->traj, pl->perm, 0, pl->n_pos, pts + 3 * q, x_ri + 2 * q);
+    } else {
+        adj_node* D = (adj_node*)calloc((size_t)pl->n_nodes, sizeof(adj_node));
+        for (i64 k = 0; k < pl->level_start[nl - 1]; ++k) {
+            const hho_node* nd = &pl->nodes[k];
+            i64 NN = nd->N[0] * nd->N[1] * nd->N[2];
+            D[k].need = (uint8_t*)calloc((size_t)NN, 1);
+            D[k].feas = (uint8_t*)calloc((size_t)NN, 1);
+            D[k].pre = (double*)calloc((size_t)4 * NN, sizeof(double));
+            D[k].adj = (double*)calloc((size_t)2 * NN, sizeof(double));
+        }
+        /* the forward's demand marking, with each needed sample's preimage kept */
+        for (i64 c = 0; c < root->nchild; ++c) {
+            const hho_node* cn = &pl->nodes[root->child0 + c];
+            node_data nd_view = {D[root->child0 + c].need, NULL};
+#pragma omp parallel for schedule(dynamic, 64)
+            for (i64 q = 0; q < n_pts; ++q) {
+                footprint F;
+                make_footprint(pl, cn, pts + 3 * q, &F);
+                mark_footprint(pl, cn, &nd_view, &F);
+            }
+        }
+        for (int l = nl - 2; l >= 0; --l) {
+            for (i64 k = pl->level_start[l]; k < pl->level_start[l + 1]; ++k) {
+                const hho_node* nd = &pl->nodes[k];
+                i64 NN = nd->N[0] * nd->N[1] * nd->N[2];
+#pragma omp parallel for schedule(dynamic, 64)
+                for (i64 li = 0; li < NN; ++li) {
+                    if (!D[k].need[li]) continue;
+                    double tgt[3], p[3];
+                    lattice_target(pl, nd, li, tgt);
+                    if (!preimage(nd->rect, nd->zbar, pl->kmin, pl->kmax, pl->zh_floor, pl->zh_mid, tgt, p)) continue;
+                    double w4[4];
+                    uvn_phi(nd->rect, nd->zbar, pl->kmin, pl->kmax, p, w4);
+                    D[k].feas[li] = 1;
+                    double* pr = D[k].pre + 4 * li;
+                    pr[0] = p[0];
+                    pr[1] = p[1];
+                    pr[2] = p[2];
+                    pr[3] = w4[3];
+                    if (l == 0) continue;
+                    for (i64 c = 0; c < nd->nchild; ++c) {
+                        footprint F;
+                        node_data nd_view = {D[nd->child0 + c].need, NULL};
+                        make_footprint(pl, &pl->nodes[nd->child0 + c], p, &F);
+                        mark_footprint(pl, &pl->nodes[nd->child0 + c], &nd_view, &F);
+                    }
+                }
+            }
+        }
+        /* final level */
+#pragma omp parallel for schedule(dynamic, 64)
+        for (i64 q = 0; q < n_pts; ++q)
+            for (i64 c = 0; c < root->nchild; ++c)
+                child_contrib_adj(pl, &A, &pl->nodes[root->child0 + c], &D[root->child0 + c], pts + 3 * q,
+                                  x_ri + 2 * q);
+        /* merges, top down, then the leaves */
+        for (int l = nl - 2; l >= 0; --l) {
+            for (i64 k = pl->level_start[l]; k < pl->level_start[l + 1]; ++k) {
+                const hho_node* nd = &pl->nodes[k];
+                i64 NN = nd->N[0] * nd->N[1] * nd->N[2];
+#pragma omp parallel for schedule(dynamic, 64)
+                for (i64 li = 0; li < NN; ++li) {
+                    if (!D[k].feas[li]) continue;
+                    const double* pr = D[k].pre + 4 * li;
+                    const double* a = D[k].adj + 2 * li;
+                    if (a[0] == 0.0 && a[1] == 0.0) continue;
+                    double cr = cos(pr[3]), ci = sin(pr[3]);
+                    double y[2] = {a[0] * cr - a[1] * ci, a[0] * ci + a[1] * cr}; /* e^{+j Phi} adj */
+                    if (l == 0) {
+                        bpa_rc_point_adj(&A, pl->traj, pl->perm, nd->begin, nd->end, pr, y);
+                    } else {
+                        for (i64 c = 0; c < nd->nchild; ++c)
+                            child_contrib_adj(pl, &A, &pl->nodes[nd->child0 + c], &D[nd->child0 + c], pr, y);
+                    }
+                }
+            }
+        }
+        for (i64 k = 0; k < pl->n_nodes; ++k) {
+            free(D[k].need);
+            free(D[k].feas);
+            free(D[k].pre);
+            free(D[k].adj);
+        }
+        free(D);
+    }
+    /* range compression: the window's bins transformed, plus the bins outside it */
+    double* tab = twiddles(A.n_fft);
+    i64 period = 2 * (i64)A.n_fft;
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < pl->n_pos; ++i)
+        for (int n = 0; n < n_f; ++n) {
+            double acc[2] = {A.extra[2 * (i * n_f + n)], A.extra[2 * (i * n_f + n) + 1]};
+            for (int j = 0; j < A.n_bins; ++j) {
+                i64 m = A.m_lo + j;
+                i64 mm = ((m % A.n_fft) + A.n_fft) % A.n_fft;
+                i64 q = ((i64)(2 * n - n_f + 1) * mm) % period;
+                if (q < 0) q += period;
+                const double* b = A.win + 2 * (i * A.n_bins + j);
+                cmac(acc, b[0], b[1], tab[2 * q], -tab[2 * q + 1]);
+            }
+            echo_ri[2 * (i * n_f + n)] = acc[0];
+            echo_ri[2 * (i * n_f + n) + 1] = acc[1];
+        }
+    free(tab);
+    free(A.win);
+    free(A.extra);
+    return 0;
+}
+
 int hho_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -408,3 +408,45 @@ def test_bpa_rc_adjoint_dot_product_identity():
     lhs = np.vdot(x, oracle.bpa_rc(s.traj, s.freqs, e, pts))
     rhs = np.vdot(oracle.bpa_rc_adjoint(s.traj, s.freqs, x, pts), e)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def _corner_points(g, k=4):
+    ix = np.r_[0:k, g.nx - k:g.nx]
+    iy = np.r_[0:k, g.ny - k:g.ny]
+    return np.array([(z * g.ny + y) * g.nx + x for z in range(g.nz) for y in iy for x in ix])
+
+
+@pytest.mark.parametrize("name,cfg,corners", [("small", dict(leaf_size=16), False),
+                                              ("small", dict(leaf_size=16, merge_factor=2), False),
+                                              ("tiny", dict(leaf_size=32, eta=1.25), True),
+                                              ("tiny", dict(leaf_size=32, eta=1.1), True)])
+def test_hhffbpa_adjoint_dot_product_identity(name, cfg, corners):
+    """<x, H s> = <H^H x, s> for the oracle's HHFFBPA and its adjoint (C, step by step); the
+    corner voxels of sparse-lattice plans take exact fallbacks and meet infeasible samples."""
+    s = synth.CONFIGS[name]()
+    rng = np.random.default_rng(4)
+    e = rng.normal(size=(len(s.traj), len(s.freqs))) + 1j * rng.normal(size=(len(s.traj), len(s.freqs)))
+    idx = _corner_points(s.grid) if corners else rng.choice(s.grid.n_vox, 40, replace=False)
+    pts = s.grid.points(idx)
+    x = rng.normal(size=len(idx)) + 1j * rng.normal(size=len(idx))
+    pl = oracle.Plan(s.traj, s.freqs, s.grid, **cfg)
+    f, st = pl.hhffbpa(e, pts)
+    if corners:
+        assert st["fallbacks"] > 0 and st["infeasible"] > 0, st
+    lhs = np.vdot(x, f)
+    rhs = np.vdot(pl.hhffbpa_adjoint(x, pts), e)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_hhffbpa_adjoint_single_level_is_bpa_rc_adjoint():
+    """With one level the HHFFBPA adjoint (C) reduces to the BPA-RC adjoint written out (numpy)."""
+    s = synth.small()
+    rng = np.random.default_rng(5)
+    idx = rng.choice(s.grid.n_vox, 30, replace=False)
+    pts = s.grid.points(idx)
+    x = rng.normal(size=30) + 1j * rng.normal(size=30)
+    pl = oracle.Plan(s.traj, s.freqs, s.grid, leaf_size=len(s.traj))
+    assert pl.info()["n_levels"] == 1
+    a = pl.hhffbpa_adjoint(x, pts)
+    b = oracle.bpa_rc_adjoint(s.traj, s.freqs, x, pts)
+    assert oracle.rel_l2(a.ravel(), b.ravel()) < 1e-12

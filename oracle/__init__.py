@@ -85,6 +85,8 @@ def _declare(L):
     L.hho_hhffbpa.restype = ctypes.c_int
     L.hho_hhffbpa_adjoint.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _dp, _i64, _dp]
     L.hho_hhffbpa_adjoint.restype = ctypes.c_int
+    L.hho_hhffbpa_traj_grad.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _dp, _dp, _i64, _dp]
+    L.hho_hhffbpa_traj_grad.restype = ctypes.c_int
     L.hho_num_threads.restype = ctypes.c_int
 
 
@@ -300,6 +302,22 @@ class Plan:
         if rc != 0:
             raise RuntimeError(f"oracle hhffbpa adjoint failed: {rc}")
         return _cplx(out, (n_pos, n_f))
+
+    def hhffbpa_traj_grad(self, echo, x, pts=None):
+        """Gradient with respect to the positions (float64 [n_pos][3]) of L = Re sum conj(x) f,
+        f = hhffbpa(echo, pts), with the plan held fixed: the leaves' and the exact fallbacks'
+        BPA-RC terms differentiated, their values y carried by the adjoint traversal."""
+        if pts is None:
+            pts = self.grid.points()
+        p = _f64(pts)
+        e = _ri(echo)
+        xr = _ri(np.asarray(x, np.complex128).ravel())
+        out = np.zeros(3 * len(self.traj))
+        rc = lib().hho_hhffbpa_traj_grad(self._h, _ptr(self.freqs), len(self.freqs), _ptr(e), _ptr(xr), _ptr(p),
+                                         len(p), _ptr(out))
+        if rc != 0:
+            raise RuntimeError(f"oracle hhffbpa traj grad failed: {rc}")
+        return out.reshape(len(self.traj), 3)
 
     def hhffbpa(self, echo, pts=None):
         """HHFFBPA values at the given points (default: all voxels).  Returns (values, stats)."""

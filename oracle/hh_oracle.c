@@ -1234,6 +1234,9 @@ typedef struct {
     double dR, kc;
     double* win;   /* [n_pos][n_bins][2]: adjoint of the profile window's bins */
     double* extra; /* [n_pos][n_f][2]: bins outside the window, transformed at once */
+    /* position-gradient mode (win and extra unused): the forward profiles and the output */
+    const hho_prof* P;
+    double* grad;  /* [n_pos][3] */
 } adj_prof;
 
 static void adj_add_bin(adj_prof* A, i64 i, i64 m, double vr, double vi) {
@@ -1261,7 +1264,10 @@ static void adj_add_bin(adj_prof* A, i64 i, i64 m, double vr, double vi) {
     }
 }
 
-/* adjoint of bpa_rc_point: value y at point p over the members perm[b..e) */
+/* adjoint of bpa_rc_point: value y at point p over the members perm[b..e).  In the
+ * position-gradient mode (A->grad set) each member instead receives
+ * Re[conj(y) e^{j 2 k_c R} (j 2 k_c lerp + (P[m0+1] - P[m0]) / dR)] (p'_i - p) / R,
+ * the derivative of the BPA-RC term with respect to p'_i paired with y. */
 static void bpa_rc_point_adj(adj_prof* A, const double* traj, const i64* perm, i64 b, i64 e, const double p[3],
                              const double y[2]) {
     for (i64 jj = b; jj < e; ++jj) {
@@ -1273,6 +1279,24 @@ static void bpa_rc_point_adj(adj_prof* A, const double* traj, const i64* perm, i
         double t = mu - fl;
         i64 m0 = (i64)fl;
         double ph = 2.0 * A->kc * R;
+        if (A->grad) {
+            double a0[2], a1[2];
+            prof_get(A->P, i, m0, a0);
+            prof_get(A->P, i, m0 + 1, a1);
+            double lr = a0[0] + t * (a1[0] - a0[0]), li = a0[1] + t * (a1[1] - a0[1]);
+            double Dr = -2.0 * A->kc * li + (a1[0] - a0[0]) / A->dR, Di = 2.0 * A->kc * lr + (a1[1] - a0[1]) / A->dR;
+            double c = cos(ph), sn = sin(ph);
+            double Er = c * Dr - sn * Di, Ei = c * Di + sn * Dr;
+            double coef = (y[0] * Er + y[1] * Ei) / R; /* Re(conj(y) E) / R; p'_i - p = -(dx, dy, dz) */
+            double* gi = A->grad + 3 * i;
+#pragma omp atomic
+            gi[0] -= coef * dx;
+#pragma omp atomic
+            gi[1] -= coef * dy;
+#pragma omp atomic
+            gi[2] -= coef * dz;
+            continue;
+        }
         double cr = cos(ph), ci = -sin(ph);
         double vr = y[0] * cr - y[1] * ci, vi = y[0] * ci + y[1] * cr; /* e^{-j ph} y */
         adj_add_bin(A, i, m0, (1.0 - t) * vr, (1.0 - t) * vi);
@@ -1317,30 +1341,18 @@ static void child_contrib_adj(const hho_plan* pl, adj_prof* A, const hho_node* c
         }
 }
 
-int hho_hhffbpa_adjoint(const hho_plan* pl, const double* freqs, int n_f, const double* x_ri, const double* pts,
-                        i64 n_pts, double* echo_ri) {
+/* The adjoint's traversal: final level, merges top down, leaves; every BPA-RC
+ * term is handed to bpa_rc_point_adj with its value y. */
+static void hhffbpa_adjoint_walk(const hho_plan* pl, adj_prof* A, const double* x_ri, const double* pts, i64 n_pts) {
     int nl = pl->n_levels;
     const hho_node* root = &pl->nodes[pl->level_start[nl - 1]];
-    double lo, hi;
-    range_bounds(pl->traj, pl->n_pos, pts, n_pts, &lo, &hi);
-    hho_prof P; /* the forward's profile window; only its bin range is used here */
-    prof_init(&P, NULL, 0, freqs, n_f, pl->os_r, lo - 0.3, hi + 0.3);
-    adj_prof A;
-    A.n_pos = pl->n_pos;
-    A.m_lo = P.m_lo;
-    A.n_bins = P.n_bins;
-    A.n_f = n_f;
-    A.n_fft = P.n_fft;
-    A.dR = P.dR;
-    A.kc = P.kc;
-    A.win = (double*)calloc((size_t)2 * pl->n_pos * P.n_bins, sizeof(double));
-    A.extra = (double*)calloc((size_t)2 * pl->n_pos * n_f, sizeof(double));
-    prof_free(&P);
-
     if (nl == 1) {
 #pragma omp parallel for schedule(dynamic, 16)
-        for (i64 q = 0; q < n_pts; ++q) bpa_rc_point_adj(&A, pl->traj, pl->perm, 0, pl->n_pos, pts + 3 * q, x_ri + 2 * q);
-    } else {
+        for (i64 q = 0; q < n_pts; ++q)
+            bpa_rc_point_adj(A, pl->traj, pl->perm, 0, pl->n_pos, pts + 3 * q, x_ri + 2 * q);
+        return;
+    }
+    {
         adj_node* D = (adj_node*)calloc((size_t)pl->n_nodes, sizeof(adj_node));
         for (i64 k = 0; k < pl->level_start[nl - 1]; ++k) {
             const hho_node* nd = &pl->nodes[k];
@@ -1393,7 +1405,7 @@ int hho_hhffbpa_adjoint(const hho_plan* pl, const double* freqs, int n_f, const 
 #pragma omp parallel for schedule(dynamic, 64)
         for (i64 q = 0; q < n_pts; ++q)
             for (i64 c = 0; c < root->nchild; ++c)
-                child_contrib_adj(pl, &A, &pl->nodes[root->child0 + c], &D[root->child0 + c], pts + 3 * q,
+                child_contrib_adj(pl, A, &pl->nodes[root->child0 + c], &D[root->child0 + c], pts + 3 * q,
                                   x_ri + 2 * q);
         /* merges, top down, then the leaves */
         for (int l = nl - 2; l >= 0; --l) {
@@ -1409,10 +1421,10 @@ int hho_hhffbpa_adjoint(const hho_plan* pl, const double* freqs, int n_f, const 
                     double cr = cos(pr[3]), ci = sin(pr[3]);
                     double y[2] = {a[0] * cr - a[1] * ci, a[0] * ci + a[1] * cr}; /* e^{+j Phi} adj */
                     if (l == 0) {
-                        bpa_rc_point_adj(&A, pl->traj, pl->perm, nd->begin, nd->end, pr, y);
+                        bpa_rc_point_adj(A, pl->traj, pl->perm, nd->begin, nd->end, pr, y);
                     } else {
                         for (i64 c = 0; c < nd->nchild; ++c)
-                            child_contrib_adj(pl, &A, &pl->nodes[nd->child0 + c], &D[nd->child0 + c], pr, y);
+                            child_contrib_adj(pl, A, &pl->nodes[nd->child0 + c], &D[nd->child0 + c], pr, y);
                     }
                 }
             }
@@ -1425,6 +1437,27 @@ int hho_hhffbpa_adjoint(const hho_plan* pl, const double* freqs, int n_f, const 
         }
         free(D);
     }
+}
+
+int hho_hhffbpa_adjoint(const hho_plan* pl, const double* freqs, int n_f, const double* x_ri, const double* pts,
+                        i64 n_pts, double* echo_ri) {
+    double lo, hi;
+    range_bounds(pl->traj, pl->n_pos, pts, n_pts, &lo, &hi);
+    hho_prof P; /* the forward's profile window; only its bin range is used here */
+    prof_init(&P, NULL, 0, freqs, n_f, pl->os_r, lo - 0.3, hi + 0.3);
+    adj_prof A;
+    memset(&A, 0, sizeof(A));
+    A.n_pos = pl->n_pos;
+    A.m_lo = P.m_lo;
+    A.n_bins = P.n_bins;
+    A.n_f = n_f;
+    A.n_fft = P.n_fft;
+    A.dR = P.dR;
+    A.kc = P.kc;
+    A.win = (double*)calloc((size_t)2 * pl->n_pos * P.n_bins, sizeof(double));
+    A.extra = (double*)calloc((size_t)2 * pl->n_pos * n_f, sizeof(double));
+    prof_free(&P);
+    hhffbpa_adjoint_walk(pl, &A, x_ri, pts, n_pts);
     /* range compression: the window's bins transformed, plus the bins outside it */
     double* tab = twiddles(A.n_fft);
     i64 period = 2 * (i64)A.n_fft;
@@ -1446,6 +1479,34 @@ int hho_hhffbpa_adjoint(const hho_plan* pl, const double* freqs, int n_f, const 
     free(tab);
     free(A.win);
     free(A.extra);
+    return 0;
+}
+
+/* Gradient with respect to the positions of L = Re sum_q conj(x_q) f(p_q), f = HHFFBPA at
+ * the points, with the plan (tree, lattices, preimages) held fixed: only the BPA-RC terms of
+ * the leaves and of the exact fallbacks depend on the positions.  The adjoint traversal
+ * carries each such term's value y; the term's derivative is taken as in the BPA-RC
+ * gradient.  grad: [n_pos][3], overwritten. */
+int hho_hhffbpa_traj_grad(const hho_plan* pl, const double* freqs, int n_f, const double* echo_ri,
+                          const double* x_ri, const double* pts, i64 n_pts, double* grad) {
+    double lo, hi;
+    range_bounds(pl->traj, pl->n_pos, pts, n_pts, &lo, &hi);
+    hho_prof P;
+    prof_init(&P, echo_ri, pl->n_pos, freqs, n_f, pl->os_r, lo - 0.3, hi + 0.3);
+    adj_prof A;
+    memset(&A, 0, sizeof(A));
+    A.n_pos = pl->n_pos;
+    A.m_lo = P.m_lo;
+    A.n_bins = P.n_bins;
+    A.n_f = n_f;
+    A.n_fft = P.n_fft;
+    A.dR = P.dR;
+    A.kc = P.kc;
+    A.P = &P;
+    A.grad = grad;
+    memset(grad, 0, sizeof(double) * 3 * (size_t)pl->n_pos);
+    hhffbpa_adjoint_walk(pl, &A, x_ri, pts, n_pts);
+    prof_free(&P);
     return 0;
 }
 

@@ -450,3 +450,35 @@ def test_hhffbpa_adjoint_single_level_is_bpa_rc_adjoint():
     a = pl.hhffbpa_adjoint(x, pts)
     b = oracle.bpa_rc_adjoint(s.traj, s.freqs, x, pts)
     assert oracle.rel_l2(a.ravel(), b.ravel()) < 1e-12
+
+
+@pytest.mark.parametrize("name,cfg,corners", [("small", dict(leaf_size=16), False),
+                                              ("tiny", dict(leaf_size=32, eta=1.25), True)])
+def test_hhffbpa_traj_grad_matches_finite_differences_with_plan_fixed(name, cfg, corners):
+    """The oracle's HHFFBPA position gradient (plan held fixed) against central differences
+    of the oracle's HHFFBPA with one position moved in place (the plan keeps its tree,
+    lattices and preimages); the corner voxels of the sparse plan take exact fallbacks."""
+    s = synth.CONFIGS[name]()
+    e = synth.scene_echo(s).numpy()
+    rng = np.random.default_rng(9)
+    idx = _corner_points(s.grid) if corners else rng.choice(s.grid.n_vox, 40, replace=False)
+    pts = s.grid.points(idx)
+    x = rng.normal(size=len(idx)) + 1j * rng.normal(size=len(idx))
+    pl = oracle.Plan(s.traj, s.freqs, s.grid, **cfg)
+    G = pl.hhffbpa_traj_grad(e, x, pts)
+    if corners:
+        assert pl.hhffbpa(e, pts)[1]["fallbacks"] > 0
+
+    def loss():
+        return (np.conj(x) * pl.hhffbpa(e, pts)[0]).real.sum()
+
+    h = 1e-9
+    for i, ax in [(0, 0), (7, 1), (33, 2), (len(s.traj) - 1, 1)]:
+        old = pl.traj[i, ax]
+        pl.traj[i, ax] = old + h
+        lp = loss()
+        pl.traj[i, ax] = old - h
+        lm = loss()
+        pl.traj[i, ax] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - G[i, ax]) <= 2e-6 * abs(G[i, ax]), (i, ax, fd, G[i, ax])

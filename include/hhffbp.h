@@ -122,9 +122,12 @@ int hhffbp_plan_info(const hh_plan* plan, hh_plan_info* info);
  *   perm[n_pos]         position index of each tree slot (members of a node are contiguous)
  *   nodes_i[n_nodes][10] {level, depth, t, begin, end, child0, nchild, N_u, N_v, N_n}
  *   nodes_d[n_nodes][11] {x'min, x'max, y'min, y'max, lo_u, lo_v, lo_n, eta_u, eta_v, eta_n, zbar}
+ *   scalars[5]          {zbar (mean height of all positions), k_min, k_max, zh_floor (least
+ *                        height of a feasible sampling point above its subarray's plane),
+ *                        zh_mid (height of D's centre above zbar: the solver's fallback depth)}
  * Nodes are ordered by level (leaves first, the root last).
  */
-int hhffbp_plan_export(const hh_plan* plan, int64_t* perm, int64_t* nodes_i, double* nodes_d);
+int hhffbp_plan_export(const hh_plan* plan, int64_t* perm, int64_t* nodes_i, double* nodes_d, double* scalars);
 
 /*
  * hhffbp_form_image -- HHFFBPA image of one scan (Sec. IV-A, Fig. 4):
@@ -233,9 +236,11 @@ int bpa_adjoint(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
 
 /*
  * bpa_form_image_noalloc -- bpa_form_image for callers that cannot allocate
- * memory during the call.  The paper has no counterpart: it is an interface
- * variant of the same computation (Eqs. eq2_rangecompression and
- * eq2_bpatimedomain), with the same arguments and results as bpa_form_image.
+ * memory during the call: code that runs under a device-memory budget fixed at
+ * start-up, or a caller whose memory pool already owns every free byte of the
+ * device.  The paper has no counterpart: it is an interface variant of the same
+ * computation (Eqs. eq2_rangecompression and eq2_bpatimedomain), with the same
+ * arguments and results as bpa_form_image.
  *
  * Workspace: a fixed device array of HH_NOALLOC_SCRATCH_BYTES per device,
  * reserved when the library's module is loaded; the call makes no device or
@@ -243,14 +248,16 @@ int bpa_adjoint(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
  * the trajectory (24 n_pos bytes) and the range profiles (16 n_pos gate_n bytes,
  * gate_n = range bins spanned by all voxel-position distances, <= n_fft), each
  * rounded up to 256 bytes.  Larger problems return HH_ERR_SCRATCH_LIMIT before
- * any device work.  The first call on a device looks the workspace up (and may
- * load the module); make it before recording a stream.
+ * any device work.  The first call on a device looks the workspace's address up
+ * (and may load the module); the cached address does not survive cudaDeviceReset.
  *
  * echo_c64 and image_c64 must be device (or managed) memory of the current
  * device (no host staging, which would need a buffer); traj_xyz and freqs_hz
  * are host arrays, copied to the workspace on cuda_stream.  Asynchronous on
  * cuda_stream.  Calls that overlap in time on the same device (any streams or
- * host threads) share the workspace and race: serialise them.
+ * host threads) share the workspace and race: serialise them.  The device
+ * counters are cleared but not read back (no synchronisation): the gate covers
+ * every voxel-position distance, so no lookup falls outside it.
  * Errors: HH_ERR_ARG (also for host or foreign-device echo/image),
  * HH_ERR_FREQ_NONUNIFORM, HH_ERR_SCRATCH_LIMIT, HH_ERR_CUDA.
  */

@@ -13,9 +13,17 @@ Parity status per function:
   ls_weights                    -- pinned (identity at integer offsets, exact on
                                    in-band tones within the least-squares bound)
   plan                          -- pinned (tree invariants, brute-force bbox)
-  hhffbpa                       -- pinned by M=1 reduction, interpolation identity,
-                                   point-target peak and the BPA bound; absolute
-                                   values are "parity unpinned" (no paper number).
+  spectral extent (lattice      -- pinned: bounded and attained, within 1/32, by an
+  density per axis)                independent evaluation of the transformed spectrum
+                                   (finite-difference Jacobian, numpy geometry) over a
+                                   superset of its probe set, and bounding the true
+                                   spectrum of every member
+  hhffbpa                       -- pinned by the M=1 reduction, the interpolation
+                                   identity, demand-driven = full evaluation, the
+                                   point-target peak and phase, and the exact (BPA-RC)
+                                   result within the accuracy bound; the paper prints
+                                   no value that fixes the absolute image
+  hhffbpa_adjoint, _traj_grad   -- pinned (dot-product identity; finite differences)
 """
 from __future__ import annotations
 

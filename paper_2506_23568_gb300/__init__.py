@@ -99,7 +99,7 @@ def _declare(L):
                               ctypes.POINTER(hh_config), vp, ctypes.POINTER(vp)]
     L.hhffbp_plan_destroy.argtypes = [vp]
     L.hhffbp_plan_info.argtypes = [vp, ctypes.POINTER(hh_plan_info)]
-    L.hhffbp_plan_export.argtypes = [vp, i64p, i64p, dp]
+    L.hhffbp_plan_export.argtypes = [vp, i64p, i64p, dp, dp]
     L.hhffbp_form_image.argtypes = [vp, vp, vp, vp]
     L.hhffbp_plan_counters.argtypes = [vp, i64p]
     i32p = ctypes.POINTER(ctypes.c_int32)
@@ -192,6 +192,38 @@ def _buffer_ptr(t):
     return ctypes.c_void_p(t.ctypes.data)
 
 
+def _checked_ptr(t, numel, what, dtype="complex64", device_only=False):
+    """Data pointer of a buffer the library reads or writes `numel` elements of, after checking
+    its element type, size and contiguity (and, when device_only, that it lives on the current
+    CUDA device): a wrong-sized buffer would otherwise be overrun by the kernels."""
+    if hasattr(t, "data_ptr"):
+        import torch
+
+        if str(t.dtype) != f"torch.{dtype}":
+            raise ValueError(f"{what}: dtype {t.dtype}, expected {dtype}")
+        if t.numel() != numel:
+            raise ValueError(f"{what}: {t.numel()} elements, expected {numel}")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        if device_only and (not t.is_cuda or t.device.index != torch.cuda.current_device()):
+            raise ValueError(f"{what}: must be a tensor on the current CUDA device")
+        return ctypes.c_void_p(t.data_ptr())
+    a = t
+    if str(a.dtype) != dtype:
+        raise ValueError(f"{what}: dtype {a.dtype}, expected {dtype}")
+    if a.size != numel:
+        raise ValueError(f"{what}: {a.size} elements, expected {numel}")
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what}: array must be C-contiguous")
+    if device_only:
+        raise ValueError(f"{what}: must be a tensor on the current CUDA device")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _n_vox(g):
+    return int(g.nx) * int(g.ny) * int(g.nz)
+
+
 class Plan:
     """A trajectory-specific HHFFBPA plan (tree + compressed sampling grids + workspace)."""
 
@@ -237,13 +269,16 @@ class Plan:
         perm = np.zeros(len(self.traj), np.int64)
         ni = np.zeros((nn, 10), np.int64)
         nd = np.zeros((nn, 11))
+        sc = np.zeros(5)
         _check(lib().hhffbp_plan_export(self._h, perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                         ni.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                        nd.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "plan_export")
+                                        nd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "plan_export")
         ls = np.concatenate([[0], np.cumsum(inf["level_nodes"])])
         return dict(perm=perm, level=ni[:, 0], depth=ni[:, 1], t=ni[:, 2], begin=ni[:, 3], end=ni[:, 4],
                     child0=ni[:, 5], nchild=ni[:, 6], N=ni[:, 7:10], rect=nd[:, :4], lo=nd[:, 4:7],
-                    eta=nd[:, 7:10], node_zbar=nd[:, 10], level_start=ls, **inf)
+                    eta=nd[:, 7:10], node_zbar=nd[:, 10], level_start=ls, zbar=sc[0], kmin=sc[1], kmax=sc[2],
+                    zh_floor=sc[3], zh_mid=sc[4], **inf)
 
     def form_image(self, echo, out=None, stream=None):
         """HHFFBPA image (complex64 [nz][ny][nx]) of echo (complex64 [n_pos][n_f]).
@@ -255,7 +290,9 @@ class Plan:
         if out is None:
             dev = echo.device if hasattr(echo, "device") else torch.device("cpu")
             out = torch.empty(self.grid.shape, dtype=torch.complex64, device=dev)
-        _check(lib().hhffbp_form_image(self._h, _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
+        n_echo = len(self.traj) * len(self.freqs)
+        _check(lib().hhffbp_form_image(self._h, _checked_ptr(echo, n_echo, "echo"),
+                                       _checked_ptr(out, _n_vox(self.grid), "out"), _stream_ptr(stream)),
                "hhffbp_form_image")
         return out
 
@@ -321,7 +358,8 @@ def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16):
         out = torch.empty(g.shape, dtype=torch.complex64, device=dev)
     _check(lib().bpa_form_image(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
                                 f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
-                                ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
+                                ctypes.byref(cfg), _checked_ptr(echo, len(t) * len(f), "echo"),
+                                _checked_ptr(out, _n_vox(g), "out"), _stream_ptr(stream)),
            "bpa_form_image")
     return out
 
@@ -343,7 +381,9 @@ def bpa_traj_gradient(traj, freqs, grid, echo, grad_image, out=None, stream=None
         out = torch.empty((len(t), 3), dtype=torch.float64, device=gi.device)
     _check(lib().bpa_traj_gradient(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
                                    f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
-                                   ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(gi), _buffer_ptr(out),
+                                   ctypes.byref(cfg), _checked_ptr(echo, len(t) * len(f), "echo"),
+                                   _checked_ptr(gi, _n_vox(g), "grad_image", device_only=True),
+                                   _checked_ptr(out, 3 * len(t), "out", dtype="float64", device_only=True),
                                    _stream_ptr(stream)),
            "bpa_traj_gradient")
     return out
@@ -364,7 +404,8 @@ def bpa_adjoint(traj, freqs, grid, image, out=None, stream=None, range_os=16):
         out = torch.empty((len(t), len(f)), dtype=torch.complex64, device=x.device)
     _check(lib().bpa_adjoint(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
                              f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
-                             ctypes.byref(cfg), _buffer_ptr(x), _buffer_ptr(out), _stream_ptr(stream)),
+                             ctypes.byref(cfg), _checked_ptr(x, _n_vox(g), "image", device_only=True),
+                             _checked_ptr(out, len(t) * len(f), "out", device_only=True), _stream_ptr(stream)),
            "bpa_adjoint")
     return out
 
@@ -412,6 +453,8 @@ def bpa_form_image_noalloc(traj, freqs, grid, echo, out, stream=None, range_os=1
     cfg = Config(range_os=range_os)
     _check(lib().bpa_form_image_noalloc(t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
                                         f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(f), ctypes.byref(g),
-                                        ctypes.byref(cfg), _buffer_ptr(echo), _buffer_ptr(out), _stream_ptr(stream)),
+                                        ctypes.byref(cfg),
+                                        _checked_ptr(echo, len(t) * len(f), "echo", device_only=True),
+                                        _checked_ptr(out, _n_vox(g), "out", device_only=True), _stream_ptr(stream)),
            "bpa_form_image_noalloc")
     return out

@@ -393,8 +393,15 @@ int hhffbp_plan_info(const hh_plan* p, hh_plan_info* info) {
     return HH_OK;
 }
 
-int hhffbp_plan_export(const hh_plan* p, int64_t* perm, int64_t* nodes_i, double* nodes_d) {
+int hhffbp_plan_export(const hh_plan* p, int64_t* perm, int64_t* nodes_i, double* nodes_d, double* scalars) {
     if (!p) return HH_ERR_ARG;
+    if (scalars) {
+        scalars[0] = p->zbar_all;
+        scalars[1] = p->kmin;
+        scalars[2] = p->kmax;
+        scalars[3] = p->zh_floor;
+        scalars[4] = p->grid.z0 + 0.5 * p->grid.dz * (p->grid.nz - 1) - p->zbar_all;
+    }
     if (perm) std::memcpy(perm, p->perm.data(), sizeof(int64_t) * p->perm.size());
     for (size_t k = 0; k < p->nodes.size(); ++k) {
         const hh::HNode& n = p->nodes[k];
@@ -532,9 +539,10 @@ int hhffbp_plan_level_counts(const hh_plan* p, int64_t* evaluated, int32_t max_l
 
 }  // extern "C"
 
-namespace {
+namespace hh {
 // Range constants and a gate of stored bins covering every (voxel, position)
-// distance: the setup of direct BPA and of its gradient.
+// distance: the setup of direct BPA, its gradient, its adjoint and the
+// fixed-workspace variant.
 void direct_bpa_setup(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
                       const hh_config* cfg, hh_plan& tmp) {
     tmp.n_pos = n_pos;
@@ -566,7 +574,7 @@ void direct_bpa_setup(const double* traj_xyz, int64_t n_pos, const double* freqs
         tmp.gate_wrap = true;
     }
 }
-}  // namespace
+}  // namespace hh
 
 extern "C" {
 
@@ -577,7 +585,7 @@ int bpa_form_image(const double* traj_xyz, int64_t n_pos, const double* freqs_hz
     if (!echo_c64 || !image_c64) return HH_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     hh_plan tmp;
-    direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
+    hh::direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
     const hh::KConst kc = hh::make_kconst(&tmp);
     std::vector<float> tw = hh::twiddle_table(tmp.n_fft);
     const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
@@ -631,7 +639,7 @@ int bpa_traj_gradient(const double* traj_xyz, int64_t n_pos, const double* freqs
     if (is_host_pointer(grad_image_c64) || is_host_pointer(grad_traj)) return HH_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     hh_plan tmp;
-    direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
+    hh::direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
     const hh::KConst kc = hh::make_kconst(&tmp);
     std::vector<float> tw = hh::twiddle_table(tmp.n_fft);
     const bool host_echo = is_host_pointer(echo_c64);
@@ -679,7 +687,7 @@ int bpa_adjoint(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     if (is_host_pointer(image_c64) || is_host_pointer(echo_c64)) return HH_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     hh_plan tmp;
-    direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
+    hh::direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
     const hh::KConst kc = hh::make_kconst(&tmp);
     std::vector<float> tw = hh::twiddle_table(tmp.n_fft);
     void *d_traj = nullptr, *d_bins = nullptr, *d_tw = nullptr, *d_cnt = nullptr;

@@ -225,5 +225,9 @@ KConst make_kconst(const hh_plan* p);
 
 // hh_api.cpp: record a CUDA error for hh_last_cuda_error() and map it to a status
 int note_cuda_error(int cuda_error);
+// hh_api.cpp: range constants and a range gate covering every (voxel, position) distance
+// (the setup of the direct-BPA entry points)
+void direct_bpa_setup(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f,
+                      const hh_grid* grid, const hh_config* cfg, hh_plan& tmp);
 
 }  // namespace hh

@@ -3,22 +3,20 @@
 // bpa_form_image obtains its workspace (trajectory copy, twiddle table, range
 // profiles, counters) with stream-ordered device allocation on every call.
 // Some callers cannot allocate at the moment they want an image: code running
-// under a memory budget that was fixed at start-up, a caller that has already
-// handed every free byte of the device to its own pool, or a stream that is
-// being recorded, where allocation calls are not allowed.  This entry point
-// serves them: its workspace is one file-scope __device__ array of fixed size,
-// reserved when this translation unit's module is loaded, and the call itself
-// performs no allocation of device or host memory.
+// under a device-memory budget that was fixed at start-up, or a caller that has
+// already handed every free byte of the device to its own memory pool.  This
+// entry point serves them: its workspace is one file-scope __device__ array of
+// fixed size, reserved when this translation unit's module is loaded, and the
+// call itself performs no allocation of device or host memory.
 //
 // The array's address is looked up once per device (with that device current)
-// on the first call; that first call may load the module and should therefore
-// happen before any stream recording starts.  There is one array per device,
-// so two calls that overlap in time on the same device (different streams or
-// host threads) race on it.
+// on the first call, which may also load the module.  The cached address does
+// not survive cudaDeviceReset (or the destruction of the device's primary
+// context).  There is one array per device, so two calls that overlap in time on
+// the same device (different streams or host threads) race on it.
 
 #include <cuda_runtime.h>
 
-#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -81,36 +79,9 @@ extern "C" int bpa_form_image_noalloc(const double* traj_xyz, int64_t n_pos, con
     if (st != HH_OK) return st;
     if (!echo_c64 || !image_c64) return HH_ERR_ARG;
     // Range constants and a gate covering every (voxel, position) distance,
-    // the same quantities bpa_form_image derives.
+    // derived exactly as bpa_form_image derives them.
     hh_plan tmp;
-    tmp.n_pos = n_pos;
-    tmp.n_f = n_f;
-    tmp.grid = *grid;
-    tmp.cfg = *cfg;
-    hh::range_constants(freqs_hz, n_f, cfg->range_os, &tmp.kmin, &tmp.kmax, &tmp.kc, &tmp.dk, &tmp.n_fft, &tmp.dR);
-    double smin = 0, smax = 0;
-    const double lo[3] = {grid->x0, grid->y0, grid->z0};
-    const double hi[3] = {grid->x0 + grid->dx * (grid->nx - 1), grid->y0 + grid->dy * (grid->ny - 1),
-                          grid->z0 + grid->dz * (grid->nz - 1)};
-    for (int i = 0; i < 3; ++i) {
-        double tl = HUGE_VAL, th = -HUGE_VAL;
-        for (int64_t q = 0; q < n_pos; ++q) {
-            tl = std::fmin(tl, traj_xyz[3 * q + i]);
-            th = std::fmax(th, traj_xyz[3 * q + i]);
-        }
-        const double gap = std::fmax(0.0, std::fmax(lo[i] - th, tl - hi[i]));
-        const double span = std::fmax(std::fabs(hi[i] - tl), std::fabs(th - lo[i]));
-        smin += gap * gap;
-        smax += span * span;
-    }
-    tmp.gate0 = (int64_t)std::floor(std::sqrt(smin) / tmp.dR) - 2;
-    tmp.gate_n = (int64_t)std::ceil(std::sqrt(smax) / tmp.dR) + 3 - tmp.gate0;
-    tmp.gate_wrap = false;
-    if (tmp.gate_n >= tmp.n_fft) {
-        tmp.gate0 = 0;
-        tmp.gate_n = tmp.n_fft;
-        tmp.gate_wrap = true;
-    }
+    hh::direct_bpa_setup(traj_xyz, n_pos, freqs_hz, n_f, grid, cfg, tmp);
     // Workspace layout: counters | twiddles | trajectory | range profiles.
     const size_t off_tw = align256(sizeof(int64_t) * hh::CNT_N);
     const size_t off_traj = off_tw + align256(sizeof(float2) * 2 * (size_t)tmp.n_fft);
@@ -135,6 +106,8 @@ extern "C" int bpa_form_image_noalloc(const double* traj_xyz, int64_t n_pos, con
     const hh::KConst kc = hh::make_kconst(&tmp);
     // The counters accumulate atomically and must start at zero; the twiddles,
     // trajectory and every gate bin of the profiles are rewritten before use.
+    // The counters are not read back (that would need a synchronisation): the gate
+    // covers every voxel-position distance, so a lookup outside it cannot occur.
     e = cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * hh::CNT_N, s);
     if (e != cudaSuccess) return hh::note_cuda_error((int)e);
     e = cudaMemcpyAsync(d_traj, traj_xyz, sizeof(double) * 3 * (size_t)n_pos, cudaMemcpyHostToDevice, s);

@@ -124,16 +124,32 @@ def test_edge_single_voxel_and_thin_grid(hh):
         assert _rel(hh.bpa_form_image(s.traj, s.freqs, g, e), bref) < REL_TOL
 
 
-def _clusters(grid, centres, half=(3, 3, 2)):
+def _cluster(grid, centre, half=(3, 3, 2)):
+    a, b, c = centre
     idx = []
-    for (a, b, c) in centres:
-        for dz in range(-half[2], half[2]):
-            for dy in range(-half[1], half[1]):
-                for dx in range(-half[0], half[0]):
-                    x, y, z = a + dx, b + dy, c + dz
-                    if 0 <= x < grid.nx and 0 <= y < grid.ny and 0 <= z < grid.nz:
-                        idx.append((z * grid.ny + y) * grid.nx + x)
+    for dz in range(-half[2], half[2]):
+        for dy in range(-half[1], half[1]):
+            for dx in range(-half[0], half[0]):
+                x, y, z = a + dx, b + dy, c + dz
+                if 0 <= x < grid.nx and 0 <= y < grid.ny and 0 <= z < grid.nz:
+                    idx.append((z * grid.ny + y) * grid.nx + x)
     return np.unique(np.array(idx))
+
+
+def _clusters(grid, centres, half=(3, 3, 2)):
+    return np.unique(np.concatenate([_cluster(grid, c, half) for c in centres]))
+
+
+def _assert_each_cluster(img, grid, centres, ref_of, what):
+    """Each voxel cluster on its own (a bright centre cannot hide an error at a corner):
+    relative L2 and max |gpu - ref| / max |ref| both within REL_TOL."""
+    for centre in centres:
+        idx = _cluster(grid, centre)
+        ref = ref_of(idx)
+        got = img.reshape(-1)[torch.as_tensor(idx, device=img.device)].cpu().numpy().astype(np.complex128)
+        rel = oracle.rel_l2(got, ref)
+        mx = np.abs(got - ref).max() / np.abs(ref).max()
+        assert rel < REL_TOL and mx < REL_TOL, (what, centre, rel, mx)
 
 
 def test_mid_sampled_parity(hh):
@@ -149,10 +165,10 @@ def test_mid_sampled_parity(hh):
     assert cnt["fallbacks_deferred"] > 0 and cnt["queue_full"] == 0, cnt
     assert torch.equal(img, plan.form_image(e).clone())
     ec = e.cpu().numpy()
-    idx = _clusters(g, [(128, 128, 32), (20, 230, 5), (250, 10, 60)])
-    ref, st = oracle.Plan(s.traj, s.freqs, g, leaf_size=64).hhffbpa(ec, g.points(idx))
-    got = img.reshape(-1)[torch.as_tensor(idx, device=img.device)].cpu().numpy()
-    assert oracle.rel_l2(got.astype(np.complex128), ref) < REL_TOL, (cnt, st)
+    centres = [(128, 128, 32), (20, 230, 5), (250, 10, 60)]
+    op = oracle.Plan(s.traj, s.freqs, g, leaf_size=64)
+    _assert_each_cluster(img, g, centres, lambda i: op.hhffbpa(ec, g.points(i))[0], ("mid", cnt))
+    idx = _clusters(g, centres)
     bi = idx[::11]
     bref = oracle.bpa_rc(s.traj, s.freqs, ec, g.points(bi))
     bimg = hh.bpa_form_image(s.traj, s.freqs, g, e)
@@ -175,10 +191,10 @@ def test_large_sampled_parity_benchmark_plan(hh):
     cnt = plan.counters()
     assert cnt["errors"] == 0 and cnt["gate_miss"] == 0 and cnt["queue_full"] == 0, cnt
     ec = e.cpu().numpy()
-    idx = _clusters(g, [(256, 256, 64), (20, 300, 120), (500, 8, 3)])
-    ref, st = oracle.Plan(s.traj, s.freqs, g, **cfg).hhffbpa(ec, g.points(idx))
-    got = img.reshape(-1)[torch.as_tensor(idx, device=img.device)].cpu().numpy()
-    assert oracle.rel_l2(got.astype(np.complex128), ref) < REL_TOL, (cnt, st)
+    centres = [(256, 256, 64), (20, 300, 120), (500, 8, 3)]
+    op = oracle.Plan(s.traj, s.freqs, g, **cfg)
+    _assert_each_cluster(img, g, centres, lambda i: op.hhffbpa(ec, g.points(i))[0], ("large", cnt))
+    idx = _clusters(g, centres)
     bimg = hh.bpa_form_image(s.traj, s.freqs, g, e)
     bi = idx[::13]
     bref = oracle.bpa_rc(s.traj, s.freqs, ec, g.points(bi))
@@ -215,3 +231,34 @@ def test_preimage_solver_matches_oracle(hh, name, cfg):
             err = np.abs(g_xyz[both] - o_xyz[both]).max(axis=1)
             # FP32 solution within the map's evaluation noise; worst near the fold
             assert np.quantile(err, 0.999) < 2e-6 and err.max() < 2e-5, (k, np.quantile(err, 0.999), err.max())
+
+
+# Range-compression variants: the decomposed FFT (k_rc_fft2) serves N_f <= 512 with
+# N_fft / M <= 32; a larger oversampling takes the shared-memory FFT (k_rc_fft, N_fft <= 8192)
+# and beyond that the direct DFT (k_rc).  A scene whose range extent exceeds the unambiguous
+# range pi / dk stores the whole period (gate wrap, indices modulo N_fft).
+RC_CASES = [("rc_fft_shared", dict(n_f=32), 64, 2048), ("rc_direct_dft", dict(n_f=32), 512, 16384),
+            ("gate_wrap", dict(n_f=8), 1, 8)]
+
+
+@pytest.mark.parametrize("what,scene_kw,range_os,n_fft", RC_CASES)
+def test_range_compression_paths_match_oracle(hh, what, scene_kw, range_os, n_fft):
+    s = synth.small(**scene_kw)
+    e = synth.scene_echo(s, device="cuda")
+    ec = e.cpu().numpy()
+    pts = s.grid.points()
+    img = hh.bpa_form_image(s.traj, s.freqs, s.grid, e, range_os=range_os)
+    torch.cuda.synchronize()
+    ref = oracle.bpa_rc(s.traj, s.freqs, ec, pts, os_r=range_os).reshape(s.grid.shape)
+    assert _rel(img, ref) < REL_TOL, what
+    cfg = dict(leaf_size=16, range_os=range_os)
+    plan = hh.Plan(s.traj, s.freqs, s.grid, **cfg)
+    info = plan.info()
+    assert info["n_fft"] == n_fft
+    if what == "gate_wrap":
+        assert info["gate_bins"] == n_fft and info["gate_start"] == 0, info
+    himg = plan.form_image(e)
+    cnt = plan.counters()
+    assert cnt["gate_miss"] == 0 and cnt["errors"] == 0, cnt
+    oref, _ = oracle.Plan(s.traj, s.freqs, s.grid, leaf_size=16, os_r=range_os).hhffbpa(ec)
+    assert _rel(himg, oref.reshape(s.grid.shape)) < REL_TOL, what

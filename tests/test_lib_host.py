@@ -50,6 +50,8 @@ def _compare_plans(ge, oe):
     np.testing.assert_allclose(ge["node_zbar"], oe["node_zbar"], rtol=0, atol=1e-15)
     np.testing.assert_allclose(ge["lo"][nonroot], oe["lo"][nonroot], rtol=1e-12, atol=1e-12)
     np.testing.assert_array_equal(ge["eta"][nonroot], oe["eta"][nonroot])
+    for k in ["zbar", "kmin", "kmax", "zh_floor", "zh_mid"]:  # the plan scalars
+        assert ge[k] == pytest.approx(oe[k], rel=1e-14, abs=1e-15), k
 
 
 @pytest.mark.parametrize("name,cfg", [("tiny", dict(leaf_size=32)), ("small", dict(leaf_size=16)),
@@ -165,3 +167,25 @@ def test_gradient_and_adjoint_refuse_null_buffers_without_cuda():
                          None) == hh.HH_ERR_ARG
     assert L.bpa_adjoint(tp, 0, fp, len(f), ctypes.byref(g), ctypes.byref(cfg), dummy, dummy,
                          None) == hh.HH_ERR_ARG
+
+
+def test_wrappers_refuse_wrong_buffers_before_any_cuda_call():
+    """The binding checks element type, element count and placement of every buffer the
+    kernels read or write before calling the library: a wrong-sized output would otherwise be
+    overrun on the device."""
+    torch = pytest.importorskip("torch")
+    s = synth.small()
+    echo = torch.zeros((len(s.traj), len(s.freqs)), dtype=torch.complex64)
+    with pytest.raises(ValueError, match="elements"):
+        hh.bpa_form_image(s.traj, s.freqs, s.grid, echo, out=torch.zeros(10, dtype=torch.complex64))
+    with pytest.raises(ValueError, match="dtype"):
+        hh.bpa_form_image(s.traj, s.freqs, s.grid, echo.to(torch.complex128),
+                          out=torch.zeros(s.grid.shape, dtype=torch.complex64))
+    with pytest.raises(ValueError, match="elements"):
+        hh.bpa_form_image(s.traj, s.freqs, s.grid, echo[:-1], out=torch.zeros(s.grid.shape, dtype=torch.complex64))
+    # the fixed-workspace variant takes device buffers of the current device only
+    with pytest.raises(ValueError, match="CUDA device"):
+        hh.bpa_form_image_noalloc(s.traj, s.freqs, s.grid, echo, torch.zeros(s.grid.shape, dtype=torch.complex64))
+    plan = hh.Plan(s.traj, s.freqs, s.grid, host_only=True, leaf_size=16)
+    with pytest.raises(ValueError, match="elements"):
+        plan.form_image(echo, out=torch.zeros(7, dtype=torch.complex64))

@@ -206,6 +206,91 @@ def test_local_spectrum_inside_unit_box_for_small_subarray():
     assert 0.9 < worst < 1.02
 
 
+def _uvn_jacobian_fd(rect, zbar, kmin, kmax, p, h=1e-6):
+    """Jacobian of (u, v, n) in (x, y, z) and grad Phi at p, by central differences of the
+    oracle's map values alone (none of its key-point algebra)."""
+    J = np.zeros((3, 3))
+    gphi = np.zeros(3)
+    for d in range(3):
+        dp = np.zeros(3)
+        dp[d] = h
+        w1 = oracle.uvn(rect, zbar, kmin, kmax, p + dp)[0]
+        w0 = oracle.uvn(rect, zbar, kmin, kmax, p - dp)[0]
+        J[:, d] = (w1[:3] - w0[:3]) / (2 * h)
+        gphi[d] = (w1[3] - w0[3]) / (2 * h)
+    return J, gphi
+
+
+def _kappa_extent(rect, zbar, kmin, kmax, pts, sources, ks):
+    """Largest |kappa_d| / pi over the points of D `pts`, the aperture points `sources` and the
+    wavenumbers `ks`: kappa = J^-T (K - grad Phi), K = 2 k (p - p') / |p - p'| (Eq. eq_kxyz_posp;
+    the spectrum-centre grad Phi of Eq. eq_dp_kc and the local-frequency transform of
+    Eq. eq_llt_spcm_trans, written here from the chain rule)."""
+    best = np.zeros(3)
+    for p in pts:
+        J, gphi = _uvn_jacobian_fd(rect, zbar, kmin, kmax, p)
+        d = p[None, :] - sources
+        u = d / np.linalg.norm(d, axis=1)[:, None]
+        K = 2.0 * np.asarray(ks)[None, :, None] * u[:, None, :]
+        kap = np.linalg.solve(J.T, (K - gphi).reshape(-1, 3).T).T
+        best = np.maximum(best, np.abs(kap).max(axis=0) / np.pi)
+    return best
+
+
+@pytest.mark.parametrize("name,cfg", [("small", dict(leaf_size=16)), ("tiny", dict(leaf_size=32)),
+                                      ("large", dict(leaf_size=256, eta=1.6))])
+def test_spectral_extent_bounds_the_subimage_spectrum(name, cfg):
+    """The per-axis lattice density eta_d = eta * rho_d (rho_d from the oracle's spectral
+    extent) against an independent evaluation of the transformed spectrum (Sec. III,
+    Eq. eq_llt_spcm_trans: the compressed subimage's local spectrum lies in a box whose
+    half-width is the sampling requirement).  For a leaf, a mid-level node and a root child:
+      (1) a superset of the oracle's probe set -- a 5x5x5 grid of D (corners, face centres and
+          centre included), the subarray border at 9 points per edge (the 1/4 steps included)
+          at the lowest and highest member heights, k_min and k_max -- bounds rho from above
+          (rho is a maximum over a subset, rounded up to 1/64) and attains it within 1/32;
+      (2) the true spectrum of the subimage -- every member's 3-D position at the extreme
+          wavenumbers (kappa is affine in k, so its extremes over [k_min, k_max] lie at the
+          ends) over the same grid of D -- stays within rho (1 + 1/32).
+    J comes from central differences of (u, v, n) and grad Phi from those of Phi, K from the
+    geometry in numpy, so a transposed solve (J kappa = ...; 2-5x off), a probe at one height
+    only (up to 8 % low on small subarrays) or a wrong spectrum centre fails here."""
+    s = synth.CONFIGS[name]()
+    ex = oracle.Plan(s.traj, s.freqs, s.grid, **cfg).export()
+    g = s.grid
+    eta0 = cfg.get("eta", 2.0)
+    ls = ex["level_start"]
+    kmin, kmax = ex["kmin"], ex["kmax"]
+    ks = np.array([kmin, kmax])
+    axes = [np.linspace(o, o + d * (n - 1), 5) for o, d, n in ((g.x0, g.dx, g.nx), (g.y0, g.dy, g.ny),
+                                                              (g.z0, g.dz, g.nz))]
+    pts = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(11)
+    for k in (0, int(ls[1]) // 2, int(ls[-2]) - 1):  # a leaf, a mid-level node, a root child
+        rect = ex["rect"][k]
+        a, b, e, gg = rect
+        zbar = ex["node_zbar"][k]
+        mem = s.traj[ex["perm"][ex["begin"][k]:ex["end"][k]]]
+        if len(mem) > 512:
+            keep = np.concatenate([rng.choice(len(mem), 500, replace=False),
+                                   np.argmin(mem, axis=0), np.argmax(mem, axis=0)])
+            mem = mem[np.unique(keep)]
+        t = np.linspace(0.0, 1.0, 9)
+        edge = np.concatenate([np.column_stack([a + t * (b - a), np.full(9, e)]),
+                               np.column_stack([a + t * (b - a), np.full(9, gg)]),
+                               np.column_stack([np.full(9, a), e + t * (gg - e)]),
+                               np.column_stack([np.full(9, b), e + t * (gg - e)])])
+        zlo, zhi = s.traj[ex["perm"][ex["begin"][k]:ex["end"][k]], 2].min(), \
+            s.traj[ex["perm"][ex["begin"][k]:ex["end"][k]], 2].max()
+        border = np.concatenate([np.column_stack([edge, np.full(len(edge), zlo)]),
+                                 np.column_stack([edge, np.full(len(edge), zhi)])])
+        rho = ex["eta"][k] / eta0
+        sup = _kappa_extent(rect, zbar, kmin, kmax, pts, border, ks)
+        true = _kappa_extent(rect, zbar, kmin, kmax, pts, mem, ks)
+        assert np.all(rho <= sup + 1.0 / 64 + 1e-6), (name, k, rho, sup)
+        assert np.all(sup <= rho * (1 + 1.0 / 32)), (name, k, rho, sup)
+        assert np.all(true <= rho * (1 + 1.0 / 32)), (name, k, rho, true)
+
+
 def test_solver_jacobian_is_llt_matrix_in_squared_height():
     """The preimage solver's Jacobian in (x, y, s = zh^2) equals the key-point matrix
     diag(-1, -1, 1) T_s (Eq. eq_duvw_relp) with its z column divided by 2 zh."""

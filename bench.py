@@ -157,10 +157,17 @@ def per_volume_s(job_ms, ranks):
     return job_ms / 1e3 / ranks
 
 
+def sm_count():
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 def roofline_of(kind, ms, units, peaks, clk_mhz):
     """(achieved, peak, unit, bound, frac) for a kernel from its algorithmic work."""
     f = clk_mhz * 1e6
-    sms = 152
+    sms = sm_count()
     if kind == "mufu":  # units = MUFU operations
         peak = MUFU_PER_SM_CLK * sms * f
         ach = units / (ms * 1e-3)
@@ -245,7 +252,8 @@ def run_gpu(args):
         ev[1].record(stream)
         hh.bpa_form_image(s.traj, s.freqs, grid, echo, out=bimg)
         ev[2].record(stream)
-        err = torch.linalg.vector_norm(img - bimg) / torch.linalg.vector_norm(bimg)
+        err = torch.linalg.vector_norm(img.to(torch.complex128) - bimg.to(torch.complex128)) / \
+            torch.linalg.vector_norm(bimg.to(torch.complex128))  # FP64 reduce
         ev[3].record(stream)
         return plan, err
 
@@ -297,8 +305,8 @@ def run_gpu(args):
     f = clk_mhz * 1e6
     roof_ms = 0.0
     for w in work:
-        t_fp = w["flop"] / (FP32_PER_SM_CLK * 152 * f)
-        t_mu = w["mufu"] / (MUFU_PER_SM_CLK * 152 * f)
+        t_fp = w["flop"] / (FP32_PER_SM_CLK * sm_count() * f)
+        t_mu = w["mufu"] / (MUFU_PER_SM_CLK * sm_count() * f)
         t_hb = w["bytes"] / (peaks["hbm_gbs"] * 1e9)
         w["roof_ms"] = 1e3 * max(t_fp, t_mu, t_hb)
         w["bound"] = ["fp32", "mufu", "hbm"][int(np.argmax([t_fp, t_mu, t_hb]))]
@@ -379,15 +387,16 @@ def run_gpu(args):
                      "traffic": TRAFFIC.get((wl, dom["stage"], dom["level"], cfg.get("leaf_size"),
                                              round(plan.config.eta, 4), plan.config.taps)),
                      "peak_source": f'{peaks["source"]} ({MUFU_PER_SM_CLK:g} SFU/clk/SM, {FP32_PER_SM_CLK:g} '
-                                    f'FLOP/clk/SM x 152 SMs at the sampled {clk_mhz:.0f} MHz)'},
+                                    f'FLOP/clk/SM x {sm_count()} SMs at the sampled {clk_mhz:.0f} MHz)'},
         "plan_ms": statistics.mean(t_plan),
         "roofline_pipeline": {"roofline_ms": roof_ms, "kernels_ms": hh_kernel_ms,
                               "frac": roof_ms / hh_kernel_ms if hh_kernel_ms else None,
                               "frac_incl_plan": roof_ms / mean_hh},
         "smem_merges": [{"stage": w["stage"], "level": w["level"], "achieved": w["smem"] / (w["ms"] * 1e-3) / 1e12,
-                         "peak": SMEM_B_PER_SM_CLK * 152 * clk_mhz * 1e6 / 1e12, "unit": "TB/s",
-                         "frac": w["smem"] / (w["ms"] * 1e-3) / (SMEM_B_PER_SM_CLK * 152 * clk_mhz * 1e6),
-                         "peak_source": f"derived ({SMEM_B_PER_SM_CLK:g} B/clk/SM x 152 SMs at {clk_mhz:.0f} MHz)"}
+                         "peak": SMEM_B_PER_SM_CLK * sm_count() * clk_mhz * 1e6 / 1e12, "unit": "TB/s",
+                         "frac": w["smem"] / (w["ms"] * 1e-3) / (SMEM_B_PER_SM_CLK * sm_count() * clk_mhz * 1e6),
+                         "peak_source": f"derived ({SMEM_B_PER_SM_CLK:g} B/clk/SM x {sm_count()} SMs at "
+                                        f"{clk_mhz:.0f} MHz)"}
                         for w in work if w["smem"] > 0],
         "roofline_bpa": {"bound": b_bound, "achieved": b_ach, "peak": b_peak, "unit": b_unit, "frac": b_frac,
                          "traffic": None},
@@ -405,70 +414,87 @@ def run_gpu(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
+        run = _oracle_run(wl, True)
+        line["cpu_baseline"] = cpu_baseline(wl, run)
+        line["cpu_baseline_bpa"] = cpu_bpa_baseline(wl)
+        # the oracle's image against the GPU image of the same scan
+        idx, ref = run[2], np.asarray(run[3])
+        got = img.reshape(-1) if idx is None else img.reshape(-1)[torch.as_tensor(idx, device=img.device)]
+        got = got.cpu().numpy().astype(np.complex128)
+        line["parity_vs_oracle"] = {
+            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_err_over_max_abs": float(np.abs(got - ref).max() / np.abs(ref).max()),
+            "voxels": int(ref.size), "tolerance": 1e-4,
+            "sample": "every voxel, same scan, same plan parameters (the oracle builds its own plan)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def _oracle_sample(wl, device=None):
-    """Bounded sample for the FP64 oracle: HHFFBPA at an 8x8x4-voxel cluster at the centre of D
-    (demand-driven), timed per phase on the host cores; returns (seconds, stats, plan export)."""
+def _oracle_points(wl, g, full):
+    """Voxels the oracle images: the whole volume, or (the reference arm's per-step sample)
+    the central half x half of the middle z-slab -- the whole slab for tiny."""
+    if full:
+        return None, "the full volume"
+    c = g.nz // 2
+    if wl == "tiny":
+        xs, ys = np.arange(g.nx), np.arange(g.ny)
+    else:
+        xs, ys = np.arange(g.nx // 4, g.nx // 4 + g.nx // 2), np.arange(g.ny // 4, g.ny // 4 + g.ny // 2)
+    idx = ((c * g.ny + ys[:, None]) * g.nx + xs[None, :]).ravel()
+    return idx, f"the central {len(xs)}x{len(ys)} voxels of z-slab {c} (1/{g.n_vox // idx.size} of D)"
+
+
+def _oracle_run(wl, full, scene=None):
+    """Time the FP64 oracle (its own plan + HHFFBPA, demand-driven, OpenMP on the host cores)
+    over the full volume or the per-step sample: (seconds, what, voxel indices, values)."""
+    import oracle
+    import synth
+
+    s, e = scene if scene is not None else (None, None)
+    if s is None:
+        s = synth.CONFIGS[wl]()
+        e = synth.scene_echo(s, device="cpu").numpy()
+    g = s.grid
+    idx, what = _oracle_points(wl, g, full)
+    pts = g.points() if idx is None else g.points(idx)
+    t0 = time.perf_counter()
+    pl = oracle.Plan(s.traj, s.freqs, g, **PLAN_CFG[wl])
+    vals, _ = pl.hhffbpa(e, pts)
+    return time.perf_counter() - t0, what, idx, vals
+
+
+def cpu_bpa_baseline(wl):
+    """The oracle's direct BPA-RC (FP64, OpenMP): the whole volume for tiny, else one z-slab
+    extrapolated to the volume (exact: its cost is the same for every voxel)."""
     import oracle
     import synth
 
     s = synth.CONFIGS[wl]()
-    if device is None:
-        try:
-            import torch
-
-            device = "cuda" if torch.cuda.is_available() else "cpu"
-        except ImportError:
-            device = "cpu"
-    e = synth.scene_echo(s, device=device).cpu().numpy()
+    e = synth.scene_echo(s, device="cpu").numpy()
     g = s.grid
-    a, b, c = g.nx // 2, g.ny // 2, g.nz // 2
-    idx = np.array([((c + dz) * g.ny + b + dy) * g.nx + a + dx for dz in range(-2, 2) for dy in range(-4, 4)
-                    for dx in range(-4, 4)])
-    pl = oracle.Plan(s.traj, s.freqs, g, **PLAN_CFG[wl])
-    ex = pl.export()
-    t0 = time.perf_counter()
-    _, st = pl.hhffbpa(e, g.points(idx))
-    return time.perf_counter() - t0, st, ex, g
-
-
-def _oracle_volume_estimate(wl):
-    """Oracle s/volume from the bounded sample: profiles as measured (they cover every
-    position), leaf BPA at the measured ns/update, merges and the final level at the
-    level-1 cost per (sample, child) interpolation, applied to the oracle plan's full
-    lattices (every subimage sample, as the paper's algorithm computes them)."""
-    t, st, ex, g = _oracle_sample(wl)
-    ls = ex["level_start"]
-    nl = len(ls) - 1
-    sizes = np.prod(ex["N"], axis=1)
-    leaf = slice(ls[0], ls[1])
-    u_leaf_all = float((sizes[leaf] * (ex["end"][leaf] - ex["begin"][leaf])).sum())
-    c_upd = st["t_levels"][0] / max(st["leaf_updates"], 1)
-    if nl > 2:
-        c_int = st["t_levels"][1] / max(st["needed_levels"][1] * int(ex["nchild"][ls[1]]), 1)
+    if wl == "tiny":
+        idx, what, scale = np.arange(g.n_vox), "the full volume, timed in full", 1.0
     else:
-        c_int = st["t_final"] / max(64 * 4 * int(ex["nchild"][ls[-2]]), 1)
-    interp_all = sum(float(sizes[ls[l]:ls[l + 1]].sum()) * int(ex["nchild"][ls[l]]) for l in range(1, nl - 1))
-    interp_all += float(g.n_vox) * int(ex["nchild"][ls[-2]])
-    est = st["t_profiles"] + c_upd * u_leaf_all + c_int * interp_all
-    sample = (f"oracle HHFFBPA (FP64, OpenMP) at an 8x8x4-voxel cluster of the {wl} workload ({t:.1f} s); "
-              f"volume = measured range profiles ({st['t_profiles']:.1f} s) + {c_upd * 1e9:.2f} ns/leaf update "
-              f"x {u_leaf_all:.3g} updates + {c_int * 1e6:.3f} us/(sample, child) x {interp_all:.3g} interpolations "
-              f"(the oracle plan's full lattices)")
-    return est, sample
+        c = g.nz // 2
+        idx = np.arange(g.nx * g.ny) + c * g.nx * g.ny
+        what, scale = f"z-slab {c} ({g.nx * g.ny} voxels), x{g.nz} to the volume (linear in voxels)", float(g.nz)
+    t0 = time.perf_counter()
+    oracle.bpa_rc(s.traj, s.freqs, e, g.points(idx))
+    t = time.perf_counter() - t0
+    return {"value": t * scale, "unit": "s/volume", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle direct BPA-RC (FP64, OpenMP) over {what}: {t:.2f} s",
+            "ns_per_update_core": t * oracle.num_threads() / (idx.size * len(s.traj)) * 1e9}
 
 
-def cpu_baseline(wl):
+def cpu_baseline(wl, run=None):
+    """The oracle over the full volume, timed in full (run = a finished _oracle_run)."""
     import oracle
 
-    est, sample = _oracle_volume_estimate(wl)
-    return {"value": est, "unit": "s/volume", "cores": oracle.num_threads(), "kind": "oracle", "sample": sample}
+    t, what, _, _ = run if run is not None else _oracle_run(wl, True)
+    return {"value": t, "unit": "s/volume", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle plan + HHFFBPA (FP64, OpenMP) over {what} of the {wl} workload, timed in full"}
 
 
 def run_reference(args):
@@ -477,18 +503,26 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    import synth
 
     wl = args.workload
+    sc = synth.CONFIGS[wl]()
+    scene = (sc, synth.scene_echo(sc, device="cpu").numpy())
+    # calibration (untimed): the full volume once, and the per-step sample once
+    t_full = _oracle_run(wl, True, scene)[0]
+    t_cal, what, _, _ = _oracle_run(wl, False, scene)
+    ratio = t_full / t_cal
     for _ in range(args.warmup):
-        _oracle_volume_estimate(wl)
+        _oracle_run(wl, False, scene)
     vals = []
     t_start = time.perf_counter()
-    sample = ""
     for _ in range(args.steps):
-        v, sample = _oracle_volume_estimate(wl)
-        vals.append(v)
+        vals.append(_oracle_run(wl, False, scene)[0] * ratio)
     wall = time.perf_counter() - t_start
     val = statistics.mean(vals)
+    sample = (f"oracle plan + HHFFBPA (FP64, OpenMP) over {what} of the {wl} workload per step, scaled by the "
+              f"measured full-volume / sample time ratio {ratio:.2f} (full volume {t_full:.1f} s, timed once "
+              f"before the warm-up)")
     line = {"metric": METRIC, "value": val, "unit": "s/volume", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -110,6 +110,17 @@ int hhffbp_interp_weights(int32_t taps, double eta, const double* tau, int64_t n
 int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, int32_t n_f, const hh_grid* grid,
                 const hh_config* cfg, void* cuda_stream, hh_plan** out);
 
+/*
+ * hhffbp_plan_update_positions -- replace the plan's positions (host float64 [n_pos][3],
+ * trajectory order) and keep everything else: tree, subarray rectangles and design planes,
+ * sampling grids, range gate.  Later calls image (and differentiate) the moved positions
+ * with that plan held fixed, as an autofocus iteration does for small corrections of an
+ * uncertain track (the paper builds one plan per scan, Sec. III).  Moves that carry a range
+ * outside the stored gate are counted (hhffbp_plan_counters).  Synchronises cuda_stream.
+ * Errors: HH_ERR_ARG (null, non-finite), HH_ERR_CUDA.
+ */
+int hhffbp_plan_update_positions(hh_plan* plan, const double* traj_xyz, void* cuda_stream);
+
 /* Release a plan and its device workspace (NULL is accepted). */
 int hhffbp_plan_destroy(hh_plan* plan);
 
@@ -162,6 +173,15 @@ int hhffbp_plan_counters(const hh_plan* plan, int64_t out[8]);
  * hhffbp_plan_counters holds the member positions summed by exact fallbacks.
  */
 int hhffbp_plan_level_counts(const hh_plan* plan, int64_t* evaluated, int32_t max_levels);
+
+/*
+ * hhffbp_plan_tile_fill -- diagnostic: synchronise and histogram, for non-root level
+ * `level` of the last form_image, the launch tiles (8 x 8 x 4 lattice samples) by the
+ * number of their samples the image needed: hist[k] = tiles with k needed samples,
+ * k = 0 .. 256 (hist has 257 entries).  Allocates, and synchronises cuda_stream.
+ * Errors: HH_ERR_ARG (null, level out of range), HH_ERR_HOST_ONLY, HH_ERR_CUDA.
+ */
+int hhffbp_plan_tile_fill(const hh_plan* plan, int32_t level, int64_t* hist, void* cuda_stream);
 
 /*
  * hhffbp_plan_profile -- when enable != 0, hhffbp_form_image records a CUDA
@@ -279,10 +299,39 @@ int hhffbp_plan_preimages(const hh_plan* plan, int64_t node, const double* targe
                           void* cuda_stream);
 
 /*
- * hhffbp_adjoint -- transpose of hhffbp_form_image (reprojection of an image to
- * echoes).  Not built yet: returns HH_ERR_UNIMPLEMENTED.
+ * hhffbp_adjoint -- the adjoint (conjugate transpose) of hhffbp_form_image as a linear map of
+ * the echo: reprojection of an image to echoes.  The paper forms images only; this is the
+ * recursion of Sec. III / Sec. IV-A (Fig. 4) transposed step by step: the final level's
+ * interpolation scattered into the root's children, the merges top down (the phase factors
+ * conjugated, the same footprints and the same exact fallbacks as the forward), the leaf
+ * backprojections (Eq. eq2_bpatimedomain) transposed into range bins, and the range
+ * compression (Eq. eq2_rangecompression) transposed.  The forward's demand passes run again
+ * (the plan's workspace is reused); no forward value is needed.
+ * image_c64: complex64 [nz][ny][nx]; echo_c64: complex64 [n_pos][n_f], overwritten; either
+ * may be device or host memory (host buffers are staged on the stream).  Asynchronous on
+ * cuda_stream.  Sums use atomics: results are not bit-reproducible between calls.  Device
+ * counters as for hhffbp_form_image (hhffbp_plan_counters).
+ * Errors: HH_ERR_ARG, HH_ERR_HOST_ONLY, HH_ERR_CUDA.
  */
 int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, void* cuda_stream);
+
+/*
+ * hhffbp_traj_gradient -- gradient with respect to the positions of a real loss L of the
+ * HHFFBPA image, with the plan held fixed (tree, sampling grids, preimages and subarray
+ * phases of the plan's trajectory; only the backprojection terms of the leaves and of the
+ * exact fallbacks move with the positions -- the paper forms images only, so this
+ * differentiates its recursion, Sec. III / Sec. IV-A, term by term).  With g the image
+ * gradient (grad_image_c64, device complex64 [nz][ny][nx], dL = Re sum_p conj(g_p) df_p), the
+ * adjoint traversal of hhffbp_adjoint carries to every such term, the value y at point p of
+ * member i, and member i receives
+ *   dL/dp'_i += Re[conj(y) exp(+j 2 k_c R) (j 2 k_c lerp_i + (P_i[m0+1] - P_i[m0]) / dR)] (p'_i - p) / R
+ * (as bpa_traj_gradient, with the range profiles of echo_c64).  grad_traj: device float64
+ * [n_pos][3] (trajectory order), overwritten.  echo_c64: device or host complex64
+ * [n_pos][n_f].  Asynchronous on cuda_stream; sums use atomics (not bit-reproducible).
+ * Errors: HH_ERR_ARG (null pointers, host gradient buffers), HH_ERR_HOST_ONLY, HH_ERR_CUDA.
+ */
+int hhffbp_traj_gradient(const hh_plan* plan, const void* echo_c64, const void* grad_image_c64, double* grad_traj,
+                         void* cuda_stream);
 
 /*
  * hh_release_cached_memory -- free the device blocks that destroyed plans left

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Grid", "Config", "Plan", "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "bpa_adjoint",
-           "bpa_image_with_offsets", "lib", "LibraryError", "status_string", "SYMBOLS"]
+           "bpa_image_with_offsets", "hhffbpa_image_with_offsets", "lib", "LibraryError", "status_string", "SYMBOLS"]
 
 HH_OK = 0
 HH_ERR_ARG = 1
@@ -37,8 +37,9 @@ HH_FLAG_HOST_ONLY = 1
 # every symbol declared in include/hhffbp.h
 SYMBOLS = ["hhffbp_default_config", "hhffbp_interp_weights", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
            "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
-           "hhffbp_plan_stage_times", "hhffbp_plan_preimages",
+           "hhffbp_plan_stage_times", "hhffbp_plan_preimages", "hhffbp_plan_tile_fill",
            "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "bpa_adjoint", "hhffbp_adjoint",
+           "hhffbp_traj_gradient", "hhffbp_plan_update_positions",
            "hh_status_string",
            "hh_last_cuda_error",
            "hh_release_cached_memory"]
@@ -105,6 +106,7 @@ def _declare(L):
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.hhffbp_plan_level_counts.argtypes = [vp, i64p, ctypes.c_int32]
     L.hhffbp_plan_preimages.argtypes = [vp, ctypes.c_int64, dp, ctypes.c_int64, dp, vp]
+    L.hhffbp_plan_tile_fill.argtypes = [vp, ctypes.c_int32, i64p, vp]
     L.hhffbp_plan_profile.argtypes = [vp, ctypes.c_int]
     L.hhffbp_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32p, i32p, ctypes.c_int32, i32p]
     L.bpa_form_image.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
@@ -114,6 +116,8 @@ def _declare(L):
     L.bpa_adjoint.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int32, ctypes.POINTER(hh_grid),
                               ctypes.POINTER(hh_config), vp, vp, vp]
     L.hhffbp_adjoint.argtypes = [vp, vp, vp, vp]
+    L.hhffbp_traj_gradient.argtypes = [vp, vp, vp, vp, vp]
+    L.hhffbp_plan_update_positions.argtypes = [vp, dp, vp]
     L.hh_status_string.argtypes = [ctypes.c_int]
     L.hh_status_string.restype = ctypes.c_char_p
     L.hh_last_cuda_error.argtypes = []
@@ -322,6 +326,14 @@ class Plan:
                "plan_level_counts")
         return out[:self.info()["n_levels"]].tolist()
 
+    def tile_fill(self, level, stream=None):
+        """Histogram (int64 [257]) of the launch tiles of a non-root level by how many of their
+        256 lattice samples the last form_image needed (synchronises)."""
+        out = np.zeros(257, np.int64)
+        _check(lib().hhffbp_plan_tile_fill(self._h, int(level), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           _stream_ptr(stream)), "plan_tile_fill")
+        return out
+
     def profile(self, enable=True):
         """Record CUDA events between the stages of each form_image."""
         _check(lib().hhffbp_plan_profile(self._h, int(bool(enable))), "plan_profile")
@@ -337,8 +349,46 @@ class Plan:
         return [(STAGE_NAMES.get(kind[i], str(kind[i])), int(lev[i]), float(ms[i])) for i in range(got.value)]
 
     def adjoint(self, image, out=None, stream=None):
-        _check(lib().hhffbp_adjoint(self._h, _buffer_ptr(image), _buffer_ptr(image), _stream_ptr(stream)),
+        """Adjoint of form_image (reprojection): complex64 [n_pos][n_f] echoes of an image
+        (complex64 [nz][ny][nx], CUDA or host).  Runs asynchronously on ``stream``."""
+        import torch
+
+        if out is None:
+            dev = image.device if hasattr(image, "device") else torch.device("cpu")
+            out = torch.empty((len(self.traj), len(self.freqs)), dtype=torch.complex64, device=dev)
+        _check(lib().hhffbp_adjoint(self._h, _checked_ptr(image, _n_vox(self.grid), "image"),
+                                    _checked_ptr(out, len(self.traj) * len(self.freqs), "out"), _stream_ptr(stream)),
                "hhffbp_adjoint")
+        return out
+
+    def update_positions(self, traj, stream=None):
+        """Replace the positions (float64 [n_pos][3]) and keep the plan: tree, sampling grids and
+        range gate of the trajectory it was built from (synchronises)."""
+        t = _f64(traj)
+        if t.shape != self.traj.shape:
+            raise ValueError(f"traj: shape {t.shape}, expected {self.traj.shape}")
+        s = ctypes.c_void_p(0) if self.config.flags & HH_FLAG_HOST_ONLY else _stream_ptr(stream)
+        _check(lib().hhffbp_plan_update_positions(self._h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), s),
+               "hhffbp_plan_update_positions")
+        self.traj = t
+
+    def traj_gradient(self, echo, grad_image, out=None, stream=None):
+        """Gradient with respect to the positions (float64 [n_pos][3], trajectory order) of a real
+        loss of form_image(echo), with the plan held fixed; grad_image is the loss's gradient with
+        respect to the image (complex64 CUDA tensor, torch's convention dL = Re sum conj(g) df)."""
+        import torch
+
+        gi = grad_image.contiguous()
+        if gi.dtype != torch.complex64:
+            gi = gi.to(torch.complex64)
+        if out is None:
+            out = torch.empty((len(self.traj), 3), dtype=torch.float64, device=gi.device)
+        _check(lib().hhffbp_traj_gradient(self._h, _checked_ptr(echo, len(self.traj) * len(self.freqs), "echo"),
+                                          _checked_ptr(gi, _n_vox(self.grid), "grad_image", device_only=True),
+                                          _checked_ptr(out, 3 * len(self.traj), "out", dtype="float64",
+                                                       device_only=True), _stream_ptr(stream)),
+               "hhffbp_traj_gradient")
+        return out
 
 
 def release_cached_memory():
@@ -433,6 +483,46 @@ def _bpa_offsets_function():
 
 
 _BPA_OFFSETS = None
+
+
+def _hh_offsets_function():
+    import torch
+
+    class _HHOffsets(torch.autograd.Function):
+        """HHFFBPA image, with a plan held fixed, of the positions nominal + offsets; the backward
+        pass is the hand-written adjoint traversal (Plan.traj_gradient)."""
+
+        @staticmethod
+        def forward(ctx, offsets, plan, nominal, echo):
+            pos = nominal + offsets.detach().cpu().numpy().astype(np.float64)
+            plan.update_positions(pos)
+            ctx.plan, ctx.pos, ctx.echo, ctx.offsets_device = plan, pos, echo, offsets.device
+            return plan.form_image(echo)
+
+        @staticmethod
+        def backward(ctx, grad_image):
+            if not np.array_equal(ctx.plan.traj, ctx.pos):  # the plan was moved since: put the positions back
+                ctx.plan.update_positions(ctx.pos)
+            g = ctx.plan.traj_gradient(ctx.echo, grad_image)
+            return g.to(ctx.offsets_device), None, None, None
+
+    return _HHOffsets
+
+
+_HH_OFFSETS = None
+
+
+def hhffbpa_image_with_offsets(offsets, plan, echo, nominal=None):
+    """Differentiable HHFFBPA image (complex64 CUDA tensor) of the positions nominal + offsets
+    (offsets a float64 tensor [n_pos][3]; autofocus of uncertain handheld tracks).  The plan --
+    tree, sampling grids and range gate of the track it was built from -- is held fixed: the
+    forward pass moves its positions (Plan.update_positions) and the backward pass is the
+    adjoint traversal (Plan.traj_gradient).  nominal defaults to the plan's current positions."""
+    global _HH_OFFSETS
+    if _HH_OFFSETS is None:
+        _HH_OFFSETS = _hh_offsets_function()
+    nom = np.array(plan.traj if nominal is None else nominal, np.float64)
+    return _HH_OFFSETS.apply(offsets, plan, nom, echo)
 
 
 def bpa_image_with_offsets(offsets, traj, freqs, grid, echo, range_os=16):

@@ -196,6 +196,31 @@ std::vector<hh::DNode> device_nodes(const hh_plan* p) {
     return out;
 }
 
+// Member positions in tree order (FP64) and, per non-root level, each member relative to the
+// centre of its node: v = centre - p' and |v|^2 / 2 (FP32), level-major.
+void member_arrays(const hh_plan* p, const std::vector<hh::DNode>& dn, std::vector<double>& mem_pos,
+                   std::vector<float>& nodev) {
+    const int64_t n_pos = p->n_pos;
+    mem_pos.assign(3 * (size_t)n_pos, 0.0);
+    for (int64_t q = 0; q < n_pos; ++q)
+        for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
+    const int n_vec_levels = std::max(1, p->n_levels - 1);
+    nodev.assign(4 * (size_t)n_pos * (size_t)n_vec_levels, 0.f);
+    const int64_t n_vec_nodes = p->n_levels > 1 ? p->level_start[p->n_levels - 1] : 0;
+    hh::parallel_for(n_vec_nodes, n_pos >= 32768 ? 16 : 1, [&](int64_t j) {  // nodes of levels 0 .. L-2
+        float* out_l = nodev.data() + 4 * (size_t)n_pos * (size_t)p->nodes[j].level;
+        const hh::DNode& L = dn[j];
+        for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
+            const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
+                        vz = (float)(L.cz - mem_pos[3 * q + 2]);
+            out_l[4 * q] = vx;
+            out_l[4 * q + 1] = vy;
+            out_l[4 * q + 2] = vz;
+            out_l[4 * q + 3] = 0.5f * std::fmaf(vx, vx, std::fmaf(vy, vy, vz * vz));
+        }
+    });
+}
+
 int upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     HH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
     return HH_OK;
@@ -278,26 +303,9 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         return HH_ERR_CUDA;
     }
     std::vector<hh::DNode> dn = device_nodes(p);
-    std::vector<double> mem_pos(3 * (size_t)n_pos);
-    for (int64_t q = 0; q < n_pos; ++q)
-        for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
-    // members relative to the centre of their node at each non-root level:
-    // v = centre - p' and |v|^2 / 2 (FP32), level-major
-    const int n_vec_levels = std::max(1, p->n_levels - 1);
-    std::vector<float> nodev(4 * (size_t)n_pos * (size_t)n_vec_levels, 0.f);
-    const int64_t n_vec_nodes = p->n_levels > 1 ? p->level_start[p->n_levels - 1] : 0;
-    hh::parallel_for(n_vec_nodes, n_pos >= 32768 ? 16 : 1, [&](int64_t j) {  // nodes of levels 0 .. L-2
-        float* out_l = nodev.data() + 4 * (size_t)n_pos * (size_t)p->nodes[j].level;
-        const hh::DNode& L = dn[j];
-        for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
-            const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
-                        vz = (float)(L.cz - mem_pos[3 * q + 2]);
-            out_l[4 * q] = vx;
-            out_l[4 * q + 1] = vy;
-            out_l[4 * q + 2] = vz;
-            out_l[4 * q + 3] = 0.5f * std::fmaf(vx, vx, std::fmaf(vy, vy, vz * vz));
-        }
-    });
+    std::vector<double> mem_pos;
+    std::vector<float> nodev;
+    member_arrays(p, dn, mem_pos, nodev);
     std::vector<float> tw = hh::twiddle_table(p->n_fft);
     const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
     HH_TRY(dev_alloc(p, &p->d_nodes, sizeof(hh::DNode) * dn.size()));
@@ -357,6 +365,23 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     p->on_device = true;
     p->last_stream = cuda_stream;
     *out = p;
+    return HH_OK;
+}
+
+int hhffbp_plan_update_positions(hh_plan* p, const double* traj_xyz, void* cuda_stream) {
+    if (!p || !traj_xyz) return HH_ERR_ARG;
+    for (int64_t q = 0; q < 3 * p->n_pos; ++q)
+        if (!std::isfinite(traj_xyz[q])) return HH_ERR_ARG;
+    p->traj.assign(traj_xyz, traj_xyz + 3 * p->n_pos);
+    if (!p->on_device) return HH_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    std::vector<double> mem_pos;
+    std::vector<float> nodev;
+    member_arrays(p, device_nodes(p), mem_pos, nodev);
+    HH_CUDA(cudaMemcpyAsync(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), cudaMemcpyHostToDevice, s));
+    HH_CUDA(cudaMemcpyAsync(p->d_nodev, nodev.data(), sizeof(float) * nodev.size(), cudaMemcpyHostToDevice, s));
+    HH_CUDA(cudaStreamSynchronize(s));  // the host arrays are released on return
+    p->last_stream = cuda_stream;
     return HH_OK;
 }
 
@@ -740,9 +765,88 @@ int hhffbp_plan_preimages(const hh_plan* p, int64_t node, const double* targets,
     return e == cudaSuccess ? HH_OK : fail_cuda(e);
 }
 
-int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, void* cuda_stream) {
-    (void)plan; (void)image_c64; (void)echo_c64; (void)cuda_stream;
-    return HH_ERR_UNIMPLEMENTED;
+int hhffbp_plan_tile_fill(const hh_plan* p, int32_t level, int64_t* hist, void* cuda_stream) {
+    if (!p || !hist) return HH_ERR_ARG;
+    if (!p->on_device) return HH_ERR_HOST_ONLY;
+    if (level < 0 || level >= p->n_levels - 1) return HH_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    void* d_h = nullptr;
+    cudaError_t e = cudaMalloc(&d_h, sizeof(int64_t) * 257);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_h, 0, sizeof(int64_t) * 257, s);
+    if (e == cudaSuccess) e = (cudaError_t)hh::launch_tile_fill(p, level, static_cast<unsigned long long*>(d_h), cuda_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hist, d_h, sizeof(int64_t) * 257, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_h);
+    return e == cudaSuccess ? HH_OK : fail_cuda(e);
+}
+
+}  // extern "C"
+
+namespace {
+// The demand passes of hhffbp_form_image (need masks and preimages of every non-root level,
+// the leaves' included) for the adjoint traversal, after clearing the counters.
+int adjoint_prologue(hh_plan* p, const hh::KConst& kc, cudaStream_t s) {
+    HH_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int64_t) * hh::CNT_N, s));
+    if (p->n_levels < 2) return HH_OK;
+    void* st = reinterpret_cast<void*>(s);
+    for (int l = 0; l + 1 < p->n_levels; ++l) HH_LAUNCH(hh::launch_tile_refs(p, kc, l, st));
+    HH_CUDA(cudaMemsetAsync(p->d_need, 0, sizeof(uint32_t) * (size_t)p->need_total, s));
+    HH_LAUNCH(hh::launch_need_final(p, kc, st));
+    for (int l = p->n_levels - 2; l >= 1; --l) HH_LAUNCH(hh::launch_need_level(p, kc, l, st));
+    HH_LAUNCH(hh::launch_need_leaf(p, kc, st));
+    return HH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int hhffbp_adjoint(const hh_plan* cp, const void* image_c64, void* echo_c64, void* cuda_stream) {
+    if (!cp || !image_c64 || !echo_c64) return HH_ERR_ARG;
+    if (!cp->on_device) return HH_ERR_HOST_ONLY;
+    hh_plan* p = const_cast<hh_plan*>(cp);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const int64_t n_vox = (int64_t)p->grid.nx * p->grid.ny * p->grid.nz;
+    const bool host_img = is_host_pointer(image_c64), host_echo = is_host_pointer(echo_c64);
+    const void* image = image_c64;
+    void* echo = echo_c64;
+    if (host_img) {
+        HH_CUDA(cudaMemcpyAsync(p->d_image_stage, image_c64, 8 * (size_t)n_vox, cudaMemcpyHostToDevice, s));
+        image = p->d_image_stage;
+    }
+    if (host_echo) echo = p->d_echo_stage;
+    const hh::KConst kc = hh::make_kconst(p);
+    if (int r = adjoint_prologue(p, kc, s)) return r;
+    // range-bin sums B_i in the profile buffer (unused by the adjoint otherwise)
+    HH_CUDA(cudaMemsetAsync(p->d_prof, 0, 8 * (size_t)p->n_pos * (size_t)(p->gate_n + 1), s));
+    HH_LAUNCH(hh::launch_adjoint_traversal(p, kc, image, p->d_prof, nullptr, cuda_stream));
+    HH_LAUNCH(hh::launch_rc_adj(p->d_prof, static_cast<const int64_t*>(p->d_perm), p->n_pos, p->n_f, p->n_fft,
+                                p->gate0, p->gate_n, p->d_twiddle, echo, cuda_stream));
+    if (host_echo)
+        HH_CUDA(cudaMemcpyAsync(echo_c64, echo, 8 * (size_t)p->n_pos * p->n_f, cudaMemcpyDeviceToHost, s));
+    p->last_stream = cuda_stream;
+    return HH_OK;
+}
+
+int hhffbp_traj_gradient(const hh_plan* cp, const void* echo_c64, const void* grad_image_c64, double* grad_traj,
+                         void* cuda_stream) {
+    if (!cp || !echo_c64 || !grad_image_c64 || !grad_traj) return HH_ERR_ARG;
+    if (!cp->on_device) return HH_ERR_HOST_ONLY;
+    if (is_host_pointer(grad_image_c64) || is_host_pointer(grad_traj)) return HH_ERR_ARG;
+    hh_plan* p = const_cast<hh_plan*>(cp);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const void* echo = echo_c64;
+    if (is_host_pointer(echo_c64)) {
+        HH_CUDA(cudaMemcpyAsync(p->d_echo_stage, echo_c64, 8 * (size_t)p->n_pos * p->n_f, cudaMemcpyHostToDevice, s));
+        echo = p->d_echo_stage;
+    }
+    const hh::KConst kc = hh::make_kconst(p);
+    if (int r = adjoint_prologue(p, kc, s)) return r;
+    HH_CUDA(cudaMemsetAsync(grad_traj, 0, sizeof(double) * 3 * (size_t)p->n_pos, s));
+    HH_LAUNCH(hh::launch_rc(echo, static_cast<const int64_t*>(p->d_perm), p->n_pos, p->n_f, p->n_fft, p->gate0,
+                            p->gate_n, p->d_twiddle, p->d_prof, nullptr, cuda_stream));
+    HH_LAUNCH(hh::launch_adjoint_traversal(p, kc, grad_image_c64, nullptr, grad_traj, cuda_stream));
+    p->last_stream = cuda_stream;
+    return HH_OK;
 }
 
 int hh_release_cached_memory(void) {

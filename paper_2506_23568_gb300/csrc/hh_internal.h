@@ -212,6 +212,15 @@ int launch_bpa_grad(const double* d_traj, int64_t n_pos, const void* d_prof, con
 int launch_bpa_adjoint(const double* d_traj, int64_t n_pos, int n_f, const KConst& kc, const hh_grid& g,
                        const void* d_img, void* d_bins, const void* d_twiddle, int n_fft, int64_t gate0, int64_t gate_n,
                        void* d_echo, void* d_counters, void* stream);
+int launch_bpa_grad_perm(const double* d_traj, int64_t n_pos, const void* d_prof, const KConst& kc, const hh_grid& g,
+                         const void* d_gimg, double* d_grad, const int64_t* d_perm, void* d_counters, void* stream);
+int launch_bpa_adjoint_bins(const double* d_traj, int64_t n_pos, const KConst& kc, const hh_grid& g, const void* d_img,
+                            void* d_bins, void* d_counters, void* stream);
+int launch_rc_adj(const void* d_bins, const int64_t* d_perm, int64_t n_pos, int n_f, int n_fft, int64_t gate0,
+                  int64_t gate_n, const void* d_twiddle, void* d_echo, void* stream);
+int launch_need_leaf(const hh_plan* p, const KConst& kc, void* stream);
+int launch_adjoint_traversal(const hh_plan* p, const KConst& kc, const void* d_img, void* d_bins, double* d_grad,
+                             void* stream);
 int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);
 int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_tile_refs(const hh_plan* p, const KConst& kc, int level, void* stream);
@@ -219,6 +228,7 @@ int launch_stage0(const hh_plan* p, const KConst& kc, void* stream);
 int launch_deferred(const hh_plan* p, const KConst& kc, int level, void* out, void* stream);
 int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_final(const hh_plan* p, const KConst& kc, void* d_image, void* stream);
+int launch_tile_fill(const hh_plan* p, int level, unsigned long long* d_hist, void* stream);
 int launch_preimage_probe(const hh_plan* p, const KConst& kc, int node, const double* d_tgt, int64_t n, double* d_out,
                           void* stream);
 KConst make_kconst(const hh_plan* p);

@@ -493,11 +493,9 @@ int build_host_plan(hh_plan* p) {
     p->need_base.assign(p->n_levels, 0);
     p->xyz_base.assign(p->n_levels, 0);
     p->need_total = p->xyz_total = 0;
-    for (int l = 0; l + 1 < p->n_levels; ++l) {
-        if (l >= 1) {
-            p->xyz_base[l] = p->xyz_total;
-            p->xyz_total += p->level_samples[l];
-        }
+    for (int l = 0; l + 1 < p->n_levels; ++l) {  // leaves too: the adjoint stores their preimages
+        p->xyz_base[l] = p->xyz_total;
+        p->xyz_total += p->level_samples[l];
     }
 
     // ---- range gate: bins covering every range a kernel can look up.  For a

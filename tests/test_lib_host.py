@@ -120,7 +120,15 @@ def test_host_only_plan_refuses_imaging():
     st = L.hhffbp_form_image(p._h, ctypes.c_void_p(buf.ctypes.data), ctypes.c_void_p(buf.ctypes.data), None)
     assert st == hh.HH_ERR_HOST_ONLY
     assert L.hhffbp_form_image(None, None, None, None) == hh.HH_ERR_ARG
-    assert L.hhffbp_adjoint(p._h, None, None, None) == hh.HH_ERR_UNIMPLEMENTED
+    assert L.hhffbp_adjoint(p._h, None, None, None) == hh.HH_ERR_ARG
+    cbuf = ctypes.c_void_p(buf.ctypes.data)
+    assert L.hhffbp_adjoint(p._h, cbuf, cbuf, None) == hh.HH_ERR_HOST_ONLY
+    assert L.hhffbp_traj_gradient(p._h, cbuf, cbuf, cbuf, None) == hh.HH_ERR_HOST_ONLY
+    # a host-only plan takes new positions without any CUDA call
+    p.update_positions(s.traj + 1e-4)
+    assert np.allclose(p.traj, s.traj + 1e-4)
+    with pytest.raises(ValueError):
+        p.update_positions(s.traj[:-1])
 
 
 @pytest.mark.parametrize("taps,eta", [(4, 2.0), (6, 1.6), (6, 1.75), (6, 2.0)])

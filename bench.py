@@ -35,12 +35,21 @@ WORKLOADS = {
     "mid": "mid: 16,384 positions (zig-zag 0.4x0.4 m, sigma 3 mm), 256 freqs, 64 points + 4 plates, "
            "256x256x64 grid, SNR 20 dB",
     "tiny": "tiny: 2,048 positions, 128 freqs, 8 points, 64x64x16 grid",
+    "sim1": "sim1 (shaped as the paper's point-scatterer simulation): 101 x 101 positions of a linear array "
+            "scanned with position/angle fluctuations (depth within 8 cm), 24 freqs 12-15 GHz, 3x3x3 points at "
+            "0.175 m pitch centred 0.4 m deep, 101x101x51 grid over 0.5 m^3",
 }
 # Plan per workload: leaf subarrays of 256 positions, 4-way merges, 6-tap LS interpolation on
 # lattices at 1.6x the measured spectral extent (-36.9 dB NRMSE vs direct BPA on large; 1.75x
 # gives -42.1 dB at 16 % more kernel time, 1.55x -35.1 dB at 6 % less).
 PLAN_CFG = {"large": dict(leaf_size=256, eta=1.6), "mid": dict(leaf_size=256, eta=1.6),
-            "tiny": dict(leaf_size=32)}
+            "tiny": dict(leaf_size=32), "sim1": dict(leaf_size=32)}
+# the paper's Table II (Sim I, one CPU core; BPA / HHFFBPA), quoted as context only
+PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
+              "centre_psf": {"bpa": [9.68, -12.77, -9.91], "hhffbpa": [9.68, -13.04, -10.63]},
+              "squint_psf": {"bpa": [11.55, -12.28, -9.90], "hhffbpa": [11.70, -12.15, -9.99]},
+              "psf_fields": ["mainlobe width mm", "PSLR dB", "ISLR dB"],
+              "hardware": "one core of a 4.5 GHz Ryzen 9 7950X, C++ without parallelisation"}
 
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
 # benchmark command on the large workload (the launch-list summary under profiles/); valid
@@ -340,6 +349,28 @@ def run_gpu(args):
     d_upd = ds.grid.n_vox * len(ds.traj)
     g_ach, g_peak, g_unit, g_bound, g_frac = roofline_of("mufu", d_ms, d_upd * BPA_MUFU, peaks, clk_mhz)
 
+    # the fast method's adjoint and plan-fixed position gradient on the same scene (leaf 64):
+    # CUDA events around each call, median of three after one warm-up call
+    dplan = hh.Plan(ds.traj, ds.freqs, ds.grid, leaf_size=64)
+    d_echo_out = torch.empty((len(ds.traj), len(ds.freqs)), dtype=torch.complex64, device="cuda")
+
+    def _timed(fn):
+        ts = []
+        for i in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    fast_adj_ms = _timed(lambda: dplan.adjoint(d_g, out=d_echo_out))
+    fast_grad_ms = _timed(lambda: dplan.traj_gradient(d_echo, d_g, out=d_out))
+    fast_fwd_ms = _timed(lambda: dplan.form_image(d_echo))
+    dplan.close()
+
     # e2e through the C ABI with pinned host buffers (H2D echo, D2H image inside the timed region)
     h_echo = echo.cpu().pin_memory()
     h_img = torch.empty(grid.shape, dtype=torch.complex64).pin_memory()
@@ -411,12 +442,22 @@ def run_gpu(args):
                               "updates": d_upd, "achieved": g_ach, "peak": g_peak, "unit": g_unit,
                               "bound": g_bound, "frac": g_frac,
                               "note": "bpa_traj_gradient incl. range compression; outside the timed steps"},
+        "fast_differentiation": {"workload": "diff: 8,192 positions, 128 freqs, 32 points, 128x128x32 grid, "
+                                               "smooth 1 mm track offsets; plan leaf 64, 4-way, 6 taps, eta 2",
+                                 "forward_ms": fast_fwd_ms, "adjoint_ms": fast_adj_ms,
+                                 "traj_gradient_ms": fast_grad_ms,
+                                 "note": "hhffbp_form_image, hhffbp_adjoint, hhffbp_traj_gradient (plan held "
+                                         "fixed); demand passes included; outside the timed steps"},
         "clocks": clk,
     }
+    if wl == "sim1":
+        line["evaluation"] = sim1_evaluation(hh, s, echo, img, bimg, cfg)
     if rank == 0 and not args.no_cpu_baseline:
         run = _oracle_run(wl, True)
         line["cpu_baseline"] = cpu_baseline(wl, run)
-        line["cpu_baseline_bpa"] = cpu_bpa_baseline(wl)
+        line["cpu_baseline_bpa"], b_idx, b_ref = cpu_bpa_baseline(wl)
+        line["precision"] = precision_study(hh, s, echo, cfg, img, bimg, run[2], np.asarray(run[3]), b_idx,
+                                            np.asarray(b_ref))
         # the oracle's image against the GPU image of the same scan
         idx, ref = run[2], np.asarray(run[3])
         got = img.reshape(-1) if idx is None else img.reshape(-1)[torch.as_tensor(idx, device=img.device)]
@@ -430,6 +471,40 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def sim1_evaluation(hh, s, echo, img, bimg, cfg):
+    """The paper's Sim-I metrics for this scan: point-spread metrics along x through the centre
+    (0, 0, 0.4) and squint (-0.175, 0, 0.4) scatterers on 0.5 mm line grids (both methods
+    imaged there directly), PSNR of HHFFBPA against direct BPA over the volume, and the time of
+    the maximum-intensity projection along z."""
+    import torch
+
+    import synth
+    from paper_2506_23568_gb300 import metrics
+
+    out = {"paper_table2_context": PAPER_SIM1}
+    for name, (x0, y0, z0) in (("centre", (0.0, 0.0, 0.4)), ("squint", (-0.175, 0.0, 0.4))):
+        lg = synth.Grid(x0 - 0.05, y0, z0, 5e-4, 1.0, 1.0, 201, 1, 1)
+        h_line = hh.Plan(s.traj, s.freqs, lg, **cfg).form_image(echo).reshape(-1).cpu().numpy()
+        b_line = hh.bpa_form_image(s.traj, s.freqs, lg, echo).reshape(-1).cpu().numpy()
+        out[f"{name}_psf"] = {"hhffbpa": [1e3 * metrics.psf_metrics(h_line, 5e-4)[0], *metrics.psf_metrics(h_line, 5e-4)[1:]],
+                              "bpa": [1e3 * metrics.psf_metrics(b_line, 5e-4)[0], *metrics.psf_metrics(b_line, 5e-4)[1:]],
+                              "fields": ["mainlobe width mm", "PSLR dB", "ISLR dB"]}
+    h, b = img.cpu().numpy(), bimg.cpu().numpy()
+    out["psnr_hhffbpa_vs_bpa_db"] = metrics.psnr_db(h, b)
+    out["psnr_magnitude_db"] = metrics.psnr_db(h, b, magnitude=True)
+    mip = hh.mip(img)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        hh.mip(img, out=mip)
+    e1.record()
+    torch.cuda.synchronize()
+    out["mip_ms"] = e0.elapsed_time(e1) / 10
+    out["note"] = ("PSF metrics on 201-sample line grids at 0.5 mm through the scatterer (the method imaged "
+                   "directly there, each with its own plan); readings of the metrics in metrics.py")
+    return out
 
 
 def _oracle_points(wl, g, full):
@@ -481,11 +556,31 @@ def cpu_bpa_baseline(wl):
         idx = np.arange(g.nx * g.ny) + c * g.nx * g.ny
         what, scale = f"z-slab {c} ({g.nx * g.ny} voxels), x{g.nz} to the volume (linear in voxels)", float(g.nz)
     t0 = time.perf_counter()
-    oracle.bpa_rc(s.traj, s.freqs, e, g.points(idx))
+    vals = oracle.bpa_rc(s.traj, s.freqs, e, g.points(idx))
     t = time.perf_counter() - t0
     return {"value": t * scale, "unit": "s/volume", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"oracle direct BPA-RC (FP64, OpenMP) over {what}: {t:.2f} s",
-            "ns_per_update_core": t * oracle.num_threads() / (idx.size * len(s.traj)) * 1e9}
+            "ns_per_update_core": t * oracle.num_threads() / (idx.size * len(s.traj)) * 1e9}, idx, vals
+
+
+def precision_study(hh, s, echo, cfg, img, bimg, h_idx, h_ref, b_idx, b_ref):
+    """Error against the FP64 oracle of the FP32 path as built (FP64 per-tile and per-node
+    references, FP32 differences) and of the same path with those references in FP32, for
+    HHFFBPA (the oracle's voxels) and direct BPA (the oracle's BPA voxels)."""
+    import torch
+
+    def rel(gpu, idx, ref):
+        g = gpu.reshape(-1) if idx is None else gpu.reshape(-1)[torch.as_tensor(idx, device=gpu.device)]
+        g = g.cpu().numpy().astype(np.complex128)
+        return float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+
+    f32 = hh.HH_FLAG_FP32_REFS
+    img32 = hh.Plan(s.traj, s.freqs, s.grid, flags=f32, **cfg).form_image(echo)
+    bimg32 = hh.bpa_form_image(s.traj, s.freqs, s.grid, echo, flags=f32)
+    return {"hhffbpa_rel_l2": {"fp64_references": rel(img, h_idx, h_ref), "fp32_references": rel(img32, h_idx, h_ref)},
+            "bpa_rel_l2": {"fp64_references": rel(bimg, b_idx, b_ref), "fp32_references": rel(bimg32, b_idx, b_ref)},
+            "note": "relative L2 against the FP64 oracle; fp32_references = HH_FLAG_FP32_REFS (per-tile reference "
+                    "ranges and phases of direct BPA and the merges' tile references in FP32)"}
 
 
 def cpu_baseline(wl, run=None):

@@ -46,6 +46,8 @@ extern "C" {
 
 /* ---- plan flags --------------------------------------------------------- */
 #define HH_FLAG_HOST_ONLY 1u      /* build tree and sampling grids on the host only (no CUDA calls) */
+#define HH_FLAG_FP32_REFS 2u      /* precision study: take the per-tile reference ranges and phases (direct BPA)
+                                     and the tile references of the merges in FP32 instead of FP64 */
 
 /* Output grid D (Sec. V: the final image grid). */
 typedef struct {
@@ -332,6 +334,15 @@ int hhffbp_adjoint(const hh_plan* plan, const void* image_c64, void* echo_c64, v
  */
 int hhffbp_traj_gradient(const hh_plan* plan, const void* echo_c64, const void* grad_image_c64, double* grad_traj,
                          void* cuda_stream);
+
+/*
+ * hh_mip -- maximum-intensity projection of a complex image (the display of the paper's
+ * reconstructions, Sec. V): out = max |f| along one axis of image_c64 (device complex64
+ * [nz][ny][nx]): axis 0 over z -> out [ny][nx], axis 1 over y -> out [nz][nx], axis 2 over
+ * x -> out [nz][ny] (device float32).  Asynchronous on cuda_stream.
+ * Errors: HH_ERR_ARG (null or host buffers, sizes <= 0, axis not 0..2), HH_ERR_CUDA.
+ */
+int hh_mip(const void* image_c64, int32_t nx, int32_t ny, int32_t nz, int32_t axis, float* out, void* cuda_stream);
 
 /*
  * hh_release_cached_memory -- free the device blocks that destroyed plans left

@@ -33,13 +33,14 @@ HH_ERR_UNIMPLEMENTED = 7
 HH_ERR_HOST_ONLY = 8
 HH_ERR_SCRATCH_LIMIT = 9
 HH_FLAG_HOST_ONLY = 1
+HH_FLAG_FP32_REFS = 2
 
 # every symbol declared in include/hhffbp.h
 SYMBOLS = ["hhffbp_default_config", "hhffbp_interp_weights", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
            "hhffbp_form_image", "hhffbp_plan_counters", "hhffbp_plan_level_counts", "hhffbp_plan_profile",
            "hhffbp_plan_stage_times", "hhffbp_plan_preimages", "hhffbp_plan_tile_fill",
            "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "bpa_adjoint", "hhffbp_adjoint",
-           "hhffbp_traj_gradient", "hhffbp_plan_update_positions",
+           "hhffbp_traj_gradient", "hhffbp_plan_update_positions", "hh_mip",
            "hh_status_string",
            "hh_last_cuda_error",
            "hh_release_cached_memory"]
@@ -118,6 +119,7 @@ def _declare(L):
     L.hhffbp_adjoint.argtypes = [vp, vp, vp, vp]
     L.hhffbp_traj_gradient.argtypes = [vp, vp, vp, vp, vp]
     L.hhffbp_plan_update_positions.argtypes = [vp, dp, vp]
+    L.hh_mip.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
     L.hh_status_string.argtypes = [ctypes.c_int]
     L.hh_status_string.restype = ctypes.c_char_p
     L.hh_last_cuda_error.argtypes = []
@@ -391,18 +393,34 @@ class Plan:
         return out
 
 
+def mip(image, axis=0, out=None, stream=None):
+    """Maximum-intensity projection max |f| of a complex64 CUDA image [nz][ny][nx] along z
+    (axis 0 -> [ny][nx]), y (axis 1 -> [nz][nx]) or x (axis 2 -> [nz][ny]); float32."""
+    import torch
+
+    nz, ny, nx = image.shape
+    shape = [(ny, nx), (nz, nx), (nz, ny)][axis]
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=image.device)
+    _check(lib().hh_mip(_checked_ptr(image, nx * ny * nz, "image", device_only=True), nx, ny, nz, int(axis),
+                        _checked_ptr(out, shape[0] * shape[1], "out", dtype="float32", device_only=True),
+                        _stream_ptr(stream)), "hh_mip")
+    return out
+
+
 def release_cached_memory():
     """Free device blocks cached by the library for reuse by later plans."""
     _check(lib().hh_release_cached_memory(), "release_cached_memory")
 
 
-def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16):
-    """Direct BPA on range-compressed data (complex64 [nz][ny][nx])."""
+def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16, flags=0):
+    """Direct BPA on range-compressed data (complex64 [nz][ny][nx]).  flags: HH_FLAG_FP32_REFS
+    takes the per-tile reference ranges and phases in FP32 (precision study)."""
     import torch
 
     t, f = _f64(traj), _f64(freqs)
     g = Grid.from_any(grid)
-    cfg = Config(range_os=range_os)
+    cfg = Config(range_os=range_os, flags=flags)
     if out is None:
         dev = echo.device if hasattr(echo, "device") else torch.device("cpu")
         out = torch.empty(g.shape, dtype=torch.complex64, device=dev)

@@ -849,6 +849,13 @@ int hhffbp_traj_gradient(const hh_plan* cp, const void* echo_c64, const void* gr
     return HH_OK;
 }
 
+int hh_mip(const void* image_c64, int32_t nx, int32_t ny, int32_t nz, int32_t axis, float* out, void* cuda_stream) {
+    if (!image_c64 || !out || nx <= 0 || ny <= 0 || nz <= 0 || axis < 0 || axis > 2) return HH_ERR_ARG;
+    if (is_host_pointer(image_c64) || is_host_pointer(out)) return HH_ERR_ARG;
+    HH_LAUNCH(hh::launch_mip(image_c64, nx, ny, nz, axis, out, cuda_stream));
+    return HH_OK;
+}
+
 int hh_release_cached_memory(void) {
     BlockCache& c = cache();
     std::lock_guard<std::mutex> lk(c.mu);

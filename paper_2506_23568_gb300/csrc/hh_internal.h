@@ -118,6 +118,7 @@ struct KConst {
     int32_t gate_n;        // stored bins per position
     int32_t wrap;          // 1 when the gate is the whole period (index modulo gate_n)
     int32_t taps;
+    int32_t fp32_refs;     // HH_FLAG_FP32_REFS: tile and node references in FP32 (precision study)
     double kc_d, kmax_d, kmin_d;  // FP64 copies for tile references
     double inv_dR_d;
 };
@@ -229,6 +230,7 @@ int launch_deferred(const hh_plan* p, const KConst& kc, int level, void* out, vo
 int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_final(const hh_plan* p, const KConst& kc, void* d_image, void* stream);
 int launch_tile_fill(const hh_plan* p, int level, unsigned long long* d_hist, void* stream);
+int launch_mip(const void* d_img, int nx, int ny, int nz, int axis, float* d_out, void* stream);
 int launch_preimage_probe(const hh_plan* p, const KConst& kc, int node, const double* d_tgt, int64_t n, double* d_out,
                           void* stream);
 KConst make_kconst(const hh_plan* p);

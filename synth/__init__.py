@@ -213,7 +213,46 @@ def diff_echo(scene, offsets, device="cpu"):
     return e.to(torch.complex64)
 
 
-CONFIGS = {"tiny": tiny, "mid": mid, "large": large, "small": small, "diff": diff}
+def _smooth(rng, n, sigma, amp):
+    """n samples of white Gaussian noise filtered by a Gaussian of sigma samples, scaled so
+    that its largest magnitude is amp."""
+    half = int(4 * sigma)
+    ker = np.exp(-0.5 * (np.arange(-half, half + 1) / sigma) ** 2)
+    x = np.convolve(rng.normal(size=n + 2 * half), ker, mode="same")[half:half + n]
+    x -= x.mean()
+    return x * (amp / np.abs(x).max())
+
+
+def sim1():
+    """Stand-in for the paper's point-scatterer simulation (Sec. V-A): a 101-element linear
+    array (along y, 4.5 mm pitch) scanned over 101 positions along x (0.45 x 0.45 m), with
+    smooth seeded fluctuations of the scan position (x +/- 5 mm), array height (+/- 1.5 cm),
+    roll about the scan axis (+/- 6.5 deg) and yaw (+/- 2 deg): element depths within 8 cm;
+    24 frequencies 12-15 GHz; a 3x3x3 lattice of unit point scatterers at 0.175 m pitch centred
+    0.4 m in front of the aperture; a 101x101x51 grid over 0.5 m^3 centred at that depth."""
+    rng = np.random.default_rng(1005)
+    n_scan, n_el = 101, 101
+    xs = np.linspace(-0.225, 0.225, n_scan)
+    ys = np.linspace(-0.225, 0.225, n_el)
+    dx = _smooth(rng, n_scan, 6.0, 5e-3)
+    dz = _smooth(rng, n_scan, 6.0, 1.5e-2)
+    roll = np.deg2rad(_smooth(rng, n_scan, 6.0, 6.5))
+    yaw = np.deg2rad(_smooth(rng, n_scan, 6.0, 2.0))
+    pts = []
+    for i in range(n_scan):
+        # element y rotated by yaw (about z) and roll (about x), then shifted
+        ex = xs[i] + dx[i] - ys * np.sin(yaw[i])
+        ey = ys * np.cos(yaw[i]) * np.cos(roll[i])
+        ez = dz[i] + ys * np.cos(yaw[i]) * np.sin(roll[i])
+        pts.append(np.column_stack([ex, ey, ez]))
+    traj = np.concatenate(pts)
+    g = np.array([-0.175, 0.0, 0.175])
+    pos = np.stack(np.meshgrid(g, g, g + 0.4, indexing="ij"), -1).reshape(-1, 3)
+    return Scene("sim1", traj, freq_list(12e9, 15e9, 24), pos, np.ones(len(pos), np.complex128),
+                 centred_grid(101, 101, 51, 5e-3, 5e-3, 1e-2, 0.15), None, 2005)
+
+
+CONFIGS = {"tiny": tiny, "mid": mid, "large": large, "small": small, "diff": diff, "sim1": sim1}
 
 
 def echoes(traj, freqs, scat_pos, scat_amp, device="cpu", max_elems=1 << 25):

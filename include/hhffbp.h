@@ -336,6 +336,26 @@ int hhffbp_traj_gradient(const hh_plan* plan, const void* echo_c64, const void* 
                          void* cuda_stream);
 
 /*
+ * Batched imaging of many independent scans (uneven lengths and grids; one plan each) by one
+ * CUDA graph launch.  The paper images one scan at a time (Sec. IV); this batches its method.
+ *   hhffbp_batch_create(plans, n_plans, n_streams, &batch): plans stay owned by the caller and
+ *     must outlive the batch; scan i runs on branch i mod n_streams of the graph, so that
+ *     independent scans execute concurrently.
+ *   hhffbp_batch_form_images(batch, echos, images, stream): echos[i] / images[i] are device
+ *     complex64 buffers of scan i (as for hhffbp_form_image).  The first call, and any call
+ *     whose buffers differ from the previous call's, records every scan's hhffbp_form_image
+ *     into a graph (relaxed stream capture on private streams: make it before the caller
+ *     starts a capture of its own); every call then launches the graph once on `stream`.
+ *     Device counters per plan as usual (hhffbp_plan_counters synchronises `stream`).
+ *   hhffbp_batch_destroy(batch) (NULL accepted).
+ * Errors: HH_ERR_ARG (null, host buffers, n <= 0), HH_ERR_HOST_ONLY, HH_ERR_OOM, HH_ERR_CUDA.
+ */
+typedef struct hh_batch hh_batch;
+int hhffbp_batch_create(hh_plan* const* plans, int32_t n_plans, int32_t n_streams, hh_batch** out);
+int hhffbp_batch_form_images(hh_batch* batch, const void* const* echos, void* const* images, void* cuda_stream);
+int hhffbp_batch_destroy(hh_batch* batch);
+
+/*
  * hh_mip -- maximum-intensity projection of a complex image (the display of the paper's
  * reconstructions, Sec. V): out = max |f| along one axis of image_c64 (device complex64
  * [nz][ny][nx]): axis 0 over z -> out [ny][nx], axis 1 over y -> out [nz][nx], axis 2 over

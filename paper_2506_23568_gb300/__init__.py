@@ -41,6 +41,7 @@ SYMBOLS = ["hhffbp_default_config", "hhffbp_interp_weights", "hhffbp_plan", "hhf
            "hhffbp_plan_stage_times", "hhffbp_plan_preimages", "hhffbp_plan_tile_fill",
            "bpa_form_image", "bpa_form_image_noalloc", "bpa_traj_gradient", "bpa_adjoint", "hhffbp_adjoint",
            "hhffbp_traj_gradient", "hhffbp_plan_update_positions", "hh_mip",
+           "hhffbp_batch_create", "hhffbp_batch_form_images", "hhffbp_batch_destroy",
            "hh_status_string",
            "hh_last_cuda_error",
            "hh_release_cached_memory"]
@@ -120,6 +121,9 @@ def _declare(L):
     L.hhffbp_traj_gradient.argtypes = [vp, vp, vp, vp, vp]
     L.hhffbp_plan_update_positions.argtypes = [vp, dp, vp]
     L.hh_mip.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
+    L.hhffbp_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)]
+    L.hhffbp_batch_form_images.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.hhffbp_batch_destroy.argtypes = [vp]
     L.hh_status_string.argtypes = [ctypes.c_int]
     L.hh_status_string.restype = ctypes.c_char_p
     L.hh_last_cuda_error.argtypes = []
@@ -391,6 +395,47 @@ class Plan:
                                                        device_only=True), _stream_ptr(stream)),
                "hhffbp_traj_gradient")
         return out
+
+
+class Batch:
+    """Many scans, one plan each, imaged by one CUDA graph launch (hhffbp_batch_*): the first
+    form_images call (and any call with other buffers) records the scans into a graph whose
+    branches run them concurrently; later calls replay it.  The plans must outlive the batch."""
+
+    def __init__(self, plans, n_streams=8):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().hhffbp_batch_create(arr, len(self.plans), int(n_streams), ctypes.byref(h)), "hhffbp_batch_create")
+        self._h = h
+
+    def form_images(self, echos, images=None, stream=None):
+        """echos: complex64 CUDA tensors [n_pos_i][n_f_i]; returns (or fills) the images."""
+        import torch
+
+        if images is None:
+            images = [torch.empty(p.grid.shape, dtype=torch.complex64, device=e.device)
+                      for p, e in zip(self.plans, echos)]
+        if len(echos) != len(self.plans) or len(images) != len(self.plans):
+            raise ValueError("one echo and one image per plan")
+        ep = (ctypes.c_void_p * len(echos))(*[_checked_ptr(e, len(p.traj) * len(p.freqs), "echo",
+                                                           device_only=True).value
+                                              for p, e in zip(self.plans, echos)])
+        ip = (ctypes.c_void_p * len(images))(*[_checked_ptr(im, _n_vox(p.grid), "image", device_only=True).value
+                                               for p, im in zip(self.plans, images)])
+        _check(lib().hhffbp_batch_form_images(self._h, ep, ip, _stream_ptr(stream)), "hhffbp_batch_form_images")
+        return images
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hhffbp_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mip(image, axis=0, out=None, stream=None):

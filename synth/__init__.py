@@ -252,6 +252,27 @@ def sim1():
                  centred_grid(101, 101, 51, 5e-3, 5e-3, 1e-2, 0.15), None, 2005)
 
 
+def batch_scene(index, seed=3000):
+    """Scan `index` of the batching workload: 4,096-32,768 positions (128 per raster line) of a
+    random-walk raster over 0.2-0.4 m (growing with the length), 128-256 frequencies
+    76-81 GHz, 16-64 unit points at z 0.22-0.38 m, a grid of 128-384 squared x 32-64 voxels
+    over the aperture and 0.2 m of depth from z = 0.2 m."""
+    rng = np.random.default_rng(seed + index)
+    n_lines = int(rng.integers(32, 257))
+    n_pos = 128 * n_lines
+    width = 0.2 + 0.2 * math.sqrt((n_pos - 4096) / (32768 - 4096))
+    traj = random_walk_raster(rng, n_lines, 128, width, width, 0.5e-3, 5e-3, 5e-3)
+    n_f = 128 + 32 * int(rng.integers(0, 5))
+    n_s = int(rng.integers(16, 65))
+    pos = np.column_stack([rng.uniform(-0.4 * width, 0.4 * width, n_s), rng.uniform(-0.4 * width, 0.4 * width, n_s),
+                           rng.uniform(0.22, 0.38, n_s)])
+    nxy = 128 + 32 * int(rng.integers(0, 9))
+    nz = 32 + 8 * int(rng.integers(0, 5))
+    d = (width + 0.05) / nxy
+    return Scene(f"batch{index}", traj, freq_list(76e9, 81e9, n_f), pos, np.ones(n_s, np.complex128),
+                 centred_grid(nxy, nxy, nz, d, d, 0.2 / nz, 0.2), None, seed + 1000 + index)
+
+
 CONFIGS = {"tiny": tiny, "mid": mid, "large": large, "small": small, "diff": diff, "sim1": sim1}
 
 

@@ -39,10 +39,13 @@ WORKLOADS = {
             "scanned with position/angle fluctuations (depth within 8 cm), 24 freqs 12-15 GHz, 3x3x3 points at "
             "0.175 m pitch centred 0.4 m deep, 101x101x51 grid over 0.5 m^3",
 }
-# Plan per workload: leaf subarrays of 256 positions, 4-way merges, 6-tap LS interpolation on
-# lattices at 1.6x the measured spectral extent (-36.9 dB NRMSE vs direct BPA on large; 1.75x
-# gives -42.1 dB at 16 % more kernel time, 1.55x -35.1 dB at 6 % less).
-PLAN_CFG = {"large": dict(leaf_size=256, eta=1.6), "mid": dict(leaf_size=256, eta=1.6),
+# Plan per workload: the autotuner's choice (paper_2506_23568_gb300.tune: the Sec. IV-B
+# operation count ranks the candidates, the cheapest are timed, acceptance at NRMSE <= -32 dB
+# against direct BPA over every 8th z-slab).  Large: leaf 256, eta 1.5, 6 taps (-33.1 dB,
+# 63.4 ms plan + image in the sweep; eta 1.6: -36.9 dB, 69.7 ms; no 4-tap plan reached
+# -32 dB at a lower cost).  Mid: leaf 512, eta 1.5 (-34.9 dB, 17.4 ms; leaf 256 eta 1.6:
+# -38.4 dB, 21.1 ms).
+PLAN_CFG = {"large": dict(leaf_size=256, eta=1.5), "mid": dict(leaf_size=512, eta=1.5),
             "tiny": dict(leaf_size=32), "sim1": dict(leaf_size=32)}
 # the paper's Table II (Sim I, one CPU core; BPA / HHFFBPA), quoted as context only
 PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
@@ -51,14 +54,12 @@ PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
               "psf_fields": ["mainlobe width mm", "PSLR dB", "ISLR dB"],
               "hardware": "one core of a 4.5 GHz Ryzen 9 7950X, C++ without parallelisation"}
 
-# DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture of the
-# benchmark command on the large workload (the launch-list summary under profiles/); valid
-# for the kernels and plan they were taken with, reported as null otherwise.
-TRAFFIC = {("large", "leaf_subimages", 0, 256, 1.6, 6): 823.7e6,
-           ("large", "merge", 1, 256, 1.6, 6): 1498.5e6,
-           ("large", "merge", 2, 256, 1.6, 6): 923.7e6,
-           ("large", "merge", 3, 256, 1.6, 6): 915.6e6,
-           ("large", "final", 4, 256, 1.6, 6): 1797.1e6}
+# DRAM bytes (read + write) per evaluated sample of a stage's kernel, from an ncu capture of
+# one launch on the mid workload (dram__bytes_read.sum + dram__bytes_write.sum = 54.4 MB +
+# 120.5 MB for 10,076,991 evaluated leaf samples; profiles/k_stage0_k_merge_mid.md), scaled to
+# a launch by the samples it evaluates; keyed by the kernel revision, null for other kernels.
+TRAFFIC_PER_SAMPLE = {("leaf_subimages", "two-sample loop, TMA windows"): 174.9e6 / 10076991}
+STAGE0_REVISION = "two-sample loop, TMA windows"
 
 # Algorithmic work per unit: a BPA-type update (one position at one point) takes one
 # rsqrt and one sincos (3 MUFU results) and about 25 FP32 operations
@@ -415,8 +416,10 @@ def run_gpu(args):
         "stages_ms": [[w["stage"], w["level"], round(w["ms"], 3), round(w["roof_ms"], 3), w["bound"]] for w in work],
         "roofline": {"kernel": f'{dom["stage"]}(level {dom["level"]})', "bound": d_bound, "achieved": d_ach,
                      "peak": d_peak, "unit": d_unit, "frac": d_frac,
-                     "traffic": TRAFFIC.get((wl, dom["stage"], dom["level"], cfg.get("leaf_size"),
-                                             round(plan.config.eta, 4), plan.config.taps)),
+                     "traffic": (TRAFFIC_PER_SAMPLE[(dom["stage"], STAGE0_REVISION)] * levels[0]
+                                 if (dom["stage"], STAGE0_REVISION) in TRAFFIC_PER_SAMPLE else None),
+                     "traffic_source": "ncu dram bytes of one launch on the mid workload, scaled by the "
+                                       "evaluated samples",
                      "peak_source": f'{peaks["source"]} ({MUFU_PER_SM_CLK:g} SFU/clk/SM, {FP32_PER_SM_CLK:g} '
                                     f'FLOP/clk/SM x {sm_count()} SMs at the sampled {clk_mhz:.0f} MHz)'},
         "plan_ms": statistics.mean(t_plan),

@@ -81,22 +81,13 @@ __device__ __forceinline__ void bpa_term_adj(const AdjOut& ao, const KConst& k, 
     }
 }
 
-// Sum of g over each segment of `seg` consecutive lanes (seg a power of two <= 32); the
-// whole warp must call it.
-__device__ __forceinline__ void segment_sum3(float g[3], int seg) {
-    for (int o = 1; o < seg; o <<= 1) {
-        g[0] += __shfl_xor_sync(0xffffffffu, g[0], o);
-        g[1] += __shfl_xor_sync(0xffffffffu, g[1], o);
-        g[2] += __shfl_xor_sync(0xffffffffu, g[2], o);
-    }
-}
-
 // Adjoint of block_fallback: for every thread with `want`, the BPA-RC adjoint (or gradient)
 // of child C's members at pc (C's frame) with value y.  The wanting threads' points are
-// compacted into slots 0 .. total-1; thread t takes point t mod n2 over the members
-// g, g + G, ... (n2 = total rounded up to a power of two, G = 256 / n2, g = t / n2); in the
-// gradient, the lanes that share a member add their terms before one FP64 atomic per axis.
-// All threads of the block must call it; scratch holds 4 x 256 float2 and s_wc 8 ints.
+// compacted into slots 0 .. total-1 (shared memory).  Adjoint: thread t takes point t mod n2
+// over the members g, g + G, ... (n2 = total rounded up to a power of two, G = 256 / n2,
+// g = t / n2) and adds each term to the member's range bins.  Gradient: a member per thread,
+// summed over all points in registers, then one FP64 atomic per axis.  All threads of the
+// block must call it; scratch holds 4 x 256 float2 and s_wc 8 ints.
 template <bool GRAD>
 __device__ void block_fallback_adj(const DNode& C, const KConst& k, bool want, float3 pc, float2 y,
                                    const float4* __restrict__ nodev, const AdjOut& ao, float2* scratch, int* s_wc,
@@ -125,32 +116,40 @@ __device__ void block_fallback_adj(const DNode& C, const KConst& k, bool want, f
         s_y[slot] = y;
     }
     __syncthreads();
+    if (GRAD) {
+        // A member per thread: its gradient is summed in registers over the block's points (read
+        // from shared memory by every lane alike), then added with one FP64 atomic per axis.
+        for (int i = C.mem_begin + (int)threadIdx.x; i < C.mem_end; i += kThreads) {
+            const float4 v = __ldg(nodev + i);
+            float g3[3] = {0.f, 0.f, 0.f};
+            for (int pt = 0; pt < total; ++pt) {
+                const float4 q = s_pt[pt];
+                const float2 ps = s_ps[pt], yv = s_y[pt];
+                float gr[3];
+                bpa_term_adj<true>(ao, k, i, v, make_float3(q.x, q.y, q.z), q.w * q.w, q.w, ps.x, ps.y, yv, gr, miss);
+                g3[0] += gr[0];
+                g3[1] += gr[1];
+                g3[2] += gr[2];
+            }
+            double* gi = ao.grad + 3 * ao.perm[i];
+            atomicAdd(gi, (double)g3[0]);
+            atomicAdd(gi + 1, (double)g3[1]);
+            atomicAdd(gi + 2, (double)g3[2]);
+        }
+        __syncthreads();  // the scratch is reused by the caller
+        return;
+    }
     int n2 = 1;
     while (n2 < total) n2 <<= 1;
     const int G = kThreads / n2;
     const int j = threadIdx.x & (n2 - 1), g = threadIdx.x / n2;
-    const int seg = n2 < 32 ? n2 : 32;
-    float4 q = make_float4(0.f, 0.f, 1.f, 1.f);
-    float2 ps = make_float2(0.f, 0.f), yy = make_float2(0.f, 0.f);
-    if (j < total) {
-        q = s_pt[j];
-        ps = s_ps[j];
-        yy = s_y[j];
-    }
-    for (int b = C.mem_begin; b < C.mem_end; b += G) {  // the same trip count in every lane
-        const int i = b + g;
-        float gr[3] = {0.f, 0.f, 0.f};
-        if (j < total && i < C.mem_end)
-            bpa_term_adj<GRAD>(ao, k, i, __ldg(nodev + i), make_float3(q.x, q.y, q.z), q.w * q.w, q.w, ps.x, ps.y,
-                               yy, gr, miss);
-        if (GRAD) {
-            segment_sum3(gr, seg);
-            if ((lane & (seg - 1)) == 0 && i < C.mem_end && (gr[0] != 0.f || gr[1] != 0.f || gr[2] != 0.f)) {
-                double* gi = ao.grad + 3 * ao.perm[i];
-                atomicAdd(gi, (double)gr[0]);
-                atomicAdd(gi + 1, (double)gr[1]);
-                atomicAdd(gi + 2, (double)gr[2]);
-            }
+    if (j < total) {  // the adjoint: a point per thread, its terms added to the members' range bins
+        const float4 q = s_pt[j];
+        const float2 ps = s_ps[j], yy = s_y[j];
+        for (int i = C.mem_begin + g; i < C.mem_end; i += G) {
+            float gr[3];
+            bpa_term_adj<false>(ao, k, i, __ldg(nodev + i), make_float3(q.x, q.y, q.z), q.w * q.w, q.w, ps.x, ps.y,
+                                yy, gr, miss);
         }
     }
     __syncthreads();  // the scratch is reused by the caller

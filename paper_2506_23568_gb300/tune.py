@@ -89,18 +89,27 @@ def _timed_ms(fn, reps=3):
     return statistics.median(ts)
 
 
-def accuracy_db(traj, freqs, grid, echo, image, every=8):
-    """NRMSE (dB) of an image against GPU direct BPA over every `every`-th z-slab of the grid."""
+def bpa_slabs(traj, freqs, grid, echo, every=8):
+    """GPU direct BPA on every `every`-th z-slab of the grid (host complex64 array)."""
     import torch
 
     from . import bpa_form_image
-    from .metrics import nrmse_db
 
-    g = type(grid)(*grid.as_tuple()) if hasattr(grid, "as_tuple") else grid
+    g = grid
     sub = g.__class__(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz * every, g.nx, g.ny, (g.nz + every - 1) // every)
     ref = bpa_form_image(traj, freqs, sub, echo)
     torch.cuda.synchronize()
-    return nrmse_db(image[::every].cpu().numpy(), ref.cpu().numpy())
+    return ref.cpu().numpy()
+
+
+def accuracy_db(traj, freqs, grid, echo, image, every=8, ref=None):
+    """NRMSE (dB) of an image against GPU direct BPA over every `every`-th z-slab of the grid
+    (ref: those slabs, when already imaged)."""
+    from .metrics import nrmse_db
+
+    if ref is None:
+        ref = bpa_slabs(traj, freqs, grid, echo, every)
+    return nrmse_db(image[::every].cpu().numpy(), ref)
 
 
 def tune(traj, freqs, grid, echo, target_db=-30.0, candidates=None, top=4, coeffs=None, every=8):
@@ -113,6 +122,7 @@ def tune(traj, freqs, grid, echo, target_db=-30.0, candidates=None, top=4, coeff
     cands = candidates or DEFAULT_CANDIDATES
     ranked = sorted(({**c, "predicted_ms": predicted_ms(op_counts(traj, freqs, grid, **c), c.get("taps", 6), coeffs)}
                      for c in cands), key=lambda r: r["predicted_ms"])
+    ref = bpa_slabs(traj, freqs, grid, echo, every)
     tried = []
     for r in ranked[:top]:
         cfg = {k: v for k, v in r.items() if k != "predicted_ms"}
@@ -123,7 +133,7 @@ def tune(traj, freqs, grid, echo, target_db=-30.0, candidates=None, top=4, coeff
             holder["img"] = holder["plan"].form_image(echo)
 
         ms = _timed_ms(run)
-        db = accuracy_db(traj, freqs, grid, echo, holder["img"], every)
+        db = accuracy_db(traj, freqs, grid, echo, holder["img"], every, ref)
         holder["plan"].close()
         tried.append({**r, "measured_ms": ms, "nrmse_db": db, "accepted": db <= target_db})
     ok = [t for t in tried if t["accepted"]]

@@ -180,12 +180,12 @@ def test_mid_sampled_parity(hh):
 
 def test_large_sampled_parity_benchmark_plan(hh):
     """Full-size large workload in the benchmark's launch configuration and plan (leaf 256,
-    eta 1.6, 6 taps): voxel clusters at the centre, an edge and a corner of the grid against
+    eta 1.5, 6 taps): voxel clusters at the centre, an edge and a corner of the grid against
     the oracle (demand-driven), a subset against the oracle's BPA-RC, and the whole volume
     against the GPU's direct BPA (-30 dB)."""
     s, e = _scene("large")
     g = s.grid
-    cfg = dict(leaf_size=256, eta=1.6)
+    cfg = dict(leaf_size=256, eta=1.5)
     plan = hh.Plan(s.traj, s.freqs, g, **cfg)
     img = plan.form_image(e)
     cnt = plan.counters()

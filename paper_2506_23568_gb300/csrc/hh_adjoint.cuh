@@ -83,11 +83,11 @@ __device__ __forceinline__ void bpa_term_adj(const AdjOut& ao, const KConst& k, 
 
 // Adjoint of block_fallback: for every thread with `want`, the BPA-RC adjoint (or gradient)
 // of child C's members at pc (C's frame) with value y.  The wanting threads' points are
-// compacted into slots 0 .. total-1 (shared memory).  Adjoint: thread t takes point t mod n2
-// over the members g, g + G, ... (n2 = total rounded up to a power of two, G = 256 / n2,
-// g = t / n2) and adds each term to the member's range bins.  Gradient: a member per thread,
-// summed over all points in registers, then one FP64 atomic per axis.  All threads of the
-// block must call it; scratch holds 4 x 256 float2 and s_wc 8 ints.
+// compacted into slots 0 .. total-1 (shared memory), and each thread takes whole members.
+// Adjoint: the points in range order, each member's terms accumulated bin by bin and added to
+// its range-bin sums once per run of a bin.  Gradient: each member's gradient summed over all
+// points in registers, then one FP64 atomic per axis.  All threads of the block must call it;
+// scratch holds 8 x 256 float2 and s_wc 8 ints.
 template <bool GRAD>
 __device__ void block_fallback_adj(const DNode& C, const KConst& k, bool want, float3 pc, float2 y,
                                    const float4* __restrict__ nodev, const AdjOut& ao, float2* scratch, int* s_wc,
@@ -139,20 +139,88 @@ __device__ void block_fallback_adj(const DNode& C, const KConst& k, bool want, f
         __syncthreads();  // the scratch is reused by the caller
         return;
     }
-    int n2 = 1;
-    while (n2 < total) n2 <<= 1;
-    const int G = kThreads / n2;
-    const int j = threadIdx.x & (n2 - 1), g = threadIdx.x / n2;
-    if (j < total) {  // the adjoint: a point per thread, its terms added to the members' range bins
-        const float4 q = s_pt[j];
-        const float2 ps = s_ps[j], yy = s_y[j];
-        for (int i = C.mem_begin + g; i < C.mem_end; i += G) {
-            float gr[3];
-            bpa_term_adj<false>(ao, k, i, __ldg(nodev + i), make_float3(q.x, q.y, q.z), q.w * q.w, q.w, ps.x, ps.y,
-                                yy, gr, miss);
+    // The adjoint: the points sorted by their range to the node centre (rank by comparison,
+    // ties by slot), then a member per thread; its terms are accumulated in two running bins
+    // (m and m + 1 of the current lerp pair) and added to the member's range-bin sums only when
+    // the bin changes, which for points in range order happens about once per bin.
+    float4* s_pt2 = reinterpret_cast<float4*>(scratch + 4 * kThreads);
+    float2* s_ps2 = scratch + 6 * kThreads;
+    float2* s_y2 = scratch + 7 * kThreads;
+    if (want) {
+        const float key = s_pt[slot].w;
+        int r = 0;
+        for (int o = 0; o < total; ++o) {
+            const float ko = s_pt[o].w;
+            r += (ko < key) || (ko == key && o < slot);
         }
+        s_pt2[r] = s_pt[slot];
+        s_ps2[r] = s_ps[slot];
+        s_y2[r] = s_y[slot];
+    }
+    __syncthreads();
+    for (int i = C.mem_begin + (int)threadIdx.x; i < C.mem_end; i += kThreads) {
+        const float4 v = __ldg(nodev + i);
+        float2* row = ao.bins + (int64_t)i * (k.gate_n + 1);
+        int cur = -2;  // bin of a0 (a1 belongs to cur + 1); -2: none
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        auto flush = [&](int m, float2 a) {
+            if (m >= 0 && (a.x != 0.f || a.y != 0.f)) {
+                atomicAdd(&row[m].x, a.x);
+                atomicAdd(&row[m].y, a.y);
+            }
+        };
+        for (int pt = 0; pt < total; ++pt) {
+            const float4 q = s_pt2[pt];
+            const float2 ps = s_ps2[pt], yv = s_y2[pt];
+            const float nh = fmaf(q.x, v.x, fmaf(q.y, v.y, fmaf(q.z, v.z, v.w)));
+            const float R2 = fmaf(2.f, nh, q.w * q.w);
+            const float yr = rsqrtf(R2);
+            const float R = R2 * yr;
+            const float d0 = R - q.w;
+            const float dR = fmaf(fmaf(-d0, fmaf(0.5f, R, 0.5f * q.w), nh), yr, d0);
+            float s, c;
+            sincos_2pi_reduced(fmaf(k.two_kc, dR, -ps.x), &s, &c);
+            const float mu = fmaf(dR, k.inv_dR, ps.y);
+            if (!k.wrap && !(mu >= 0.f && mu < (float)(k.gate_n - 1))) {  // outside the stored gate: not expected
+                ++miss;
+                continue;
+            }
+            const float fl = floorf(mu);
+            const float t = mu - fl;
+            int m = (int)fl;
+            if (k.wrap) m &= (k.gate_n - 1);
+            const float2 cv = make_float2(fmaf(yv.x, c, yv.y * s), fmaf(yv.y, c, -yv.x * s));  // e^{-j th} y
+            if (m != cur) {
+                if (m == cur + 1) {  // the pair moved up one bin: a0 is complete
+                    flush(cur, a0);
+                    a0 = a1;
+                } else {
+                    flush(cur, a0);
+                    flush(cur + 1, a1);
+                    a0 = make_float2(0.f, 0.f);
+                }
+                a1 = make_float2(0.f, 0.f);
+                cur = m;
+            }
+            a0.x = fmaf(1.f - t, cv.x, a0.x);
+            a0.y = fmaf(1.f - t, cv.y, a0.y);
+            a1.x = fmaf(t, cv.x, a1.x);
+            a1.y = fmaf(t, cv.y, a1.y);
+        }
+        flush(cur, a0);
+        flush(cur + 1, a1);
     }
     __syncthreads();  // the scratch is reused by the caller
+}
+
+// w x (|w x| < 2^26) rounded to an integer in the FMA pipe: the multiple of 16 nearest to
+// w x by the magic constant 1.5 * 2^27 (whose ulp is 16), then the exact residual (one FMA,
+// |.| <= 8) by kRoundMagic.
+__device__ __forceinline__ int fixed_term(float w, float x) {
+    constexpr float kMagic27 = 201326592.0f;  // 1.5 * 2^27
+    const float hb = fmaf(w, x, kMagic27);
+    const float r = fmaf(w, x, -(hb - kMagic27));
+    return (__float_as_int(hb) - __float_as_int(kMagic27)) * 16 + (__float_as_int(r + kRoundMagic) - (int)kRoundBits);
 }
 
 // Adjoint of interp_children: for every active thread, each child's term of the forward,
@@ -160,19 +228,36 @@ __device__ void block_fallback_adj(const DNode& C, const KConst& k, bool want, f
 // receive w e^{-j ph_c} y.  The union boxes of the active threads' footprints are staged from
 // the children's target pool (0 at needed, feasible samples, NaN elsewhere, plus what other
 // blocks have added so far) with the forward's geometry, so that a footprint is complete
-// exactly when the forward's is; complete footprints scatter into the zeroed box with
-// shared-memory atomics, and every non-zero box sample is then added to the pool with one
-// global atomic.  Children whose footprint is incomplete are flagged in fb_mask (bit ci) for
-// the adjoint of the exact fallback.  All threads must call it.
+// exactly when the forward's is; complete footprints scatter into the zeroed box, and every
+// non-zero box sample is then added to the pool with one global atomic.  Children whose
+// footprint is incomplete are flagged in fb_mask (bit ci) for the adjoint of the exact
+// fallback.  All threads must call it.
+//
+// The box accumulates in 32-bit fixed point with integer shared-memory atomics (order-free
+// sums, no retry loop under contention).  With max(|Re y| + |Im y|) < 2^e over the block's
+// threads and tap weights of magnitude at most 1 (the least-squares weights peak at 1, at
+// integer delays), a term times S = 2^(26 - e) is below 2^26 and is rounded to an integer
+// (fixed_term): a resolution of 2^-26 of the block's largest value, near the FP32 rounding of
+// the terms.  A box sample receives at most one term per thread, and in practice the sums
+// stay far below 2^31; every atomic checks its own addition for a signed wrap, and a pass in
+// which one wrapped is zeroed and scattered again at S = 2^(22 - e), where 256 terms stay
+// below 2^30.  A non-finite y makes every staged box sample NaN.
 template <int TAPS, bool LATTICE>
 __device__ void adj_children(const DNode* __restrict__ nodes, int child0, int nch, float2* __restrict__ tpool,
                              const WPoly& wp, float2* s_stage, int* s_box, StageGeo* s_geo, bool active,
                              const float* s_wph, float2 y, unsigned& fb_mask) {
+    static_assert(kThreads <= 256, "fixed-point box sums assume at most 256 terms per sample");
     __shared__ int s_npass;
+    __shared__ unsigned s_ymax;
     for (int i = threadIdx.x; i < 6 * kMaxChild; i += blockDim.x) s_box[i] = (i % 6) < 3 ? INT_MAX : INT_MIN;
+    if (threadIdx.x == 0) s_ymax = 0u;
     fb_mask = 0u;
     __syncthreads();
     const int t = threadIdx.x;
+    {  // block maximum of |Re y| + |Im y| (non-negative floats order as their bits)
+        const unsigned m = __reduce_max_sync(0xffffffffu, active ? __float_as_uint(fabsf(y.x) + fabsf(y.y)) : 0u);
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_ymax, m);
+    }
     for (int ci = 0; ci < nch; ++ci) {
         const float wq[3] = {s_wph[(4 * ci + 0) * kThreads + t], s_wph[(4 * ci + 1) * kThreads + t],
                              s_wph[(4 * ci + 2) * kThreads + t]};
@@ -226,6 +311,12 @@ __device__ void adj_children(const DNode* __restrict__ nodes, int child0, int nc
     }
     __syncthreads();
     const int npass = s_npass;
+    int2* s_acc = reinterpret_cast<int2*>(s_stage);  // the boxes in fixed point
+    const float ymax = __uint_as_float(s_ymax);
+    const bool finite = ymax <= FLT_MAX;
+    int ex = 0;
+    frexpf(finite ? ymax : 1.f, &ex);  // ymax < 2^ex
+    const int sh = max(-122, min(126, 26 - ex));  // the fine scale; sh - 4 the safe one
     for (int ps = 0; ps < npass; ++ps) {
         // 1. stage this pass's boxes from the target pool (their NaN marks decide completeness)
         for (int ci = 0; ci < nch; ++ci) {
@@ -271,55 +362,80 @@ __device__ void adj_children(const DNode* __restrict__ nodes, int child0, int nc
             }
         }
         __syncthreads();
-        // 2. zero the staged boxes, 3. scatter the complete footprints into them
-        for (int ci = 0; ci < nch; ++ci) {
-            const StageGeo& g = s_geo[ci];
-            if (g.pass != ps || !g.staged) continue;
-            for (int i = threadIdx.x; i < g.n[0] * g.p1; i += blockDim.x) s_stage[g.off + i] = make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        for (int ci = 0; ci < nch; ++ci) {
-            if (!((ok_mask >> ci) & 1u)) continue;
-            const StageGeo& g = s_geo[ci];
-            const DNode& C = nodes[child0 + ci];
-            const float wc[3] = {s_wph[(4 * ci + 0) * kThreads + t], s_wph[(4 * ci + 1) * kThreads + t],
-                                 s_wph[(4 * ci + 2) * kThreads + t]};
-            float wt[3][TAPS];
-            int base[3];
-            footprint<TAPS>(C, wp, wc, wt, base);
-            float sn, cs;
-            sincos_2pi_reduced(s_wph[(4 * ci + 3) * kThreads + t], &sn, &cs);
-            const float2 v = make_float2(fmaf(y.x, cs, y.y * sn), fmaf(y.y, cs, -y.x * sn));  // e^{-j ph} y
-            for (int i0 = 0; i0 < TAPS; ++i0)
-                for (int i1 = 0; i1 < TAPS; ++i1) {
-                    const float w01 = wt[0][i0] * wt[1][i1];
+        // 2. zero the staged boxes, 3. scatter the complete footprints into them (once more at the
+        // safe scale if a fine-scale sum wrapped; the unstaged children go to the pool directly,
+        // in the first round only)
+        int shp = sh;
+        for (int round = 0; round < 2; ++round, shp = sh - 4) {
+            for (int ci = 0; ci < nch; ++ci) {
+                const StageGeo& g = s_geo[ci];
+                if (g.pass != ps || !g.staged) continue;
+                for (int i = threadIdx.x; i < g.n[0] * g.p1; i += blockDim.x) s_acc[g.off + i] = make_int2(0, 0);
+            }
+            __syncthreads();
+            const float scale = __int_as_float((127 + shp) << 23);
+            int wrap = 0;  // sign bit set when one of this thread's atomic additions wrapped
+            for (int ci = 0; ci < nch; ++ci) {
+                if (!((ok_mask >> ci) & 1u)) continue;
+                const StageGeo& g = s_geo[ci];
+                if (round > 0 && !g.staged) continue;
+                const DNode& C = nodes[child0 + ci];
+                const float wc[3] = {s_wph[(4 * ci + 0) * kThreads + t], s_wph[(4 * ci + 1) * kThreads + t],
+                                     s_wph[(4 * ci + 2) * kThreads + t]};
+                float wt[3][TAPS];
+                int base[3];
+                footprint<TAPS>(C, wp, wc, wt, base);
+                float sn, cs;
+                sincos_2pi_reduced(s_wph[(4 * ci + 3) * kThreads + t], &sn, &cs);
+                const float2 v = make_float2(fmaf(y.x, cs, y.y * sn), fmaf(y.y, cs, -y.x * sn));  // e^{-j ph} y
+                if (g.staged) {
+                    const float2 vs = make_float2(v.x * scale, v.y * scale);
+                    int2* box = s_acc + g.off + (base[0] - g.lo[0]) * g.p1 + (base[1] - g.lo[1]) * g.p2 + (base[2] - g.lo[2]);
+                    for (int i0 = 0; i0 < TAPS; ++i0)
+                        for (int i1 = 0; i1 < TAPS; ++i1) {
+                            const float w01 = wt[0][i0] * wt[1][i1];
+                            int2* row = box + i0 * g.p1 + i1 * g.p2;
 #pragma unroll
-                    for (int i2 = 0; i2 < TAPS; ++i2) {
-                        const float w = w01 * wt[2][i2];
-                        float2* dst =
-                            g.staged ? s_stage + g.off + (base[0] - g.lo[0] + i0) * g.p1 + (base[1] - g.lo[1] + i1) * g.p2 +
-                                           (base[2] - g.lo[2] + i2)
-                                     : tpool + C.pool_off + ((int64_t)(base[0] + i0) * C.N[1] + base[1] + i1) * C.N[2] +
-                                           base[2] + i2;
-                        atomicAdd(&dst->x, w * v.x);
-                        atomicAdd(&dst->y, w * v.y);
-                    }
+                            for (int i2 = 0; i2 < TAPS; ++i2) {
+                                const float w = w01 * wt[2][i2];
+                                const int qx = fixed_term(w, vs.x), qy = fixed_term(w, vs.y);
+                                const int ox = atomicAdd(&row[i2].x, qx), oy = atomicAdd(&row[i2].y, qy);
+                                const int sx = (int)((unsigned)ox + (unsigned)qx), sy = (int)((unsigned)oy + (unsigned)qy);
+                                wrap |= ((sx ^ ox) & (sx ^ qx)) | ((sy ^ oy) & (sy ^ qy));
+                            }
+                        }
+                } else {
+                    for (int i0 = 0; i0 < TAPS; ++i0)
+                        for (int i1 = 0; i1 < TAPS; ++i1) {
+                            const float w01 = wt[0][i0] * wt[1][i1];
+                            float2* row = tpool + C.pool_off +
+                                          ((int64_t)(base[0] + i0) * C.N[1] + base[1] + i1) * C.N[2] + base[2];
+#pragma unroll
+                            for (int i2 = 0; i2 < TAPS; ++i2) {
+                                const float w = w01 * wt[2][i2];
+                                atomicAdd(&row[i2].x, w * v.x);
+                                atomicAdd(&row[i2].y, w * v.y);
+                            }
+                        }
                 }
+            }
+            if (!__syncthreads_or(wrap < 0)) break;
         }
-        __syncthreads();
         // 4. add the boxes to the pool
+        const float unscale = __int_as_float((127 - shp) << 23);
         for (int ci = 0; ci < nch; ++ci) {
             const StageGeo& g = s_geo[ci];
             if (g.pass != ps || !g.staged) continue;
             const DNode& C = nodes[child0 + ci];
             float2* dstp = tpool + C.pool_off;
             for (BoxWalk it(g.n[1], g.n[2]); it.q0 < g.n[0]; it.next()) {
-                const float2 v = s_stage[g.off + it.q0 * g.p1 + it.q1 * g.p2 + it.q2];
-                if (v.x != 0.f || v.y != 0.f) {
+                const int2 q = s_acc[g.off + it.q0 * g.p1 + it.q1 * g.p2 + it.q2];
+                if (q.x != 0 || q.y != 0 || !finite) {
                     float2* d = dstp + ((int64_t)(g.lo[0] + it.q0) * C.N[1] + (g.lo[1] + it.q1)) * C.N[2] +
                                 (g.lo[2] + it.q2);
-                    atomicAdd(&d->x, v.x);
-                    atomicAdd(&d->y, v.y);
+                    const float nan = __int_as_float(0x7fc00000);
+                    atomicAdd(&d->x, finite ? (float)q.x * unscale : nan);
+                    atomicAdd(&d->y, finite ? (float)q.y * unscale : nan);
                 }
             }
         }
@@ -513,7 +629,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_adj(const DNode* __restrict__
                                                       const uint32_t* __restrict__ need,
                                                       const float4* __restrict__ xyz, AdjOut ao,
                                                       unsigned long long* cnt) {
-    __shared__ float2 s_scr[4 * kThreads];
+    __shared__ float2 s_scr[8 * kThreads];
     __shared__ int s_wc[kThreads / 32];
     const DTile tile = tile_of(tm, nodes);
     const DNode n = nodes[tile.node];

@@ -486,9 +486,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_final_adj(const DNode* __restri
                  czv = 0.5 * (min(tile.o2 + kTile2 - 1, g.nz - 1) - tile.o2);
     const double ptx = g.x0 + (tile.o0 + cxv) * g.dx, pty = g.y0 + (tile.o1 + cyv) * g.dy,
                  ptz = g.z0 + (tile.o2 + czv) * g.dz;
-    if ((int)threadIdx.x < nch) {
-        make_ref(nodes[child0 + threadIdx.x], k, ptx, pty, ptz, s_ref[threadIdx.x]);
-        s_phase[threadIdx.x] = (float)mod_2pi(s_ref[threadIdx.x].phi);
+    if ((int)threadIdx.x < 4 * nch) {  // the forward's references (k_final)
+        const int ci = threadIdx.x >> 2;
+        make_ref_quad(nodes[child0 + ci], k, ptx, pty, ptz, quad_mask(nch), s_ref[ci]);
+        if ((threadIdx.x & 3) == 0) s_phase[ci] = (float)mod_2pi(s_ref[ci].phi);
     }
     __syncthreads();
     const float3 dl = make_float3((float)((lx - cxv) * g.dx), (float)((ly - cyv) * g.dy), (float)((lz - czv) * g.dz));
@@ -575,11 +576,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_merge_adj(const DNode* __restri
         return;
     }
     if (!any) return;  // block-uniform
-    if ((int)threadIdx.x <= nch) {
+    if ((int)threadIdx.x < 4 * (nch + 1)) {  // the forward's references (k_merge)
         const float3 pt = s_pt;
         const double px = P.cx + (double)pt.x, py = P.cy + (double)pt.y, pz = P.cz + (double)pt.z;
-        const DNode& X = threadIdx.x == 0 ? P : nodes[P.child0 + threadIdx.x - 1];
-        make_ref(X, k, px, py, pz, s_ref[threadIdx.x]);
+        const int xi = threadIdx.x >> 2;
+        const DNode& X = xi == 0 ? P : nodes[P.child0 + xi - 1];
+        make_ref_quad(X, k, px, py, pz, quad_mask(nch + 1), s_ref[xi]);
     }
     __syncthreads();
     if (threadIdx.x >= 1 && (int)threadIdx.x <= nch)

@@ -127,7 +127,7 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz, &p->d_nodev, &p->d_tile_ref, &p->d_prof2,
+                     &p->d_need, &p->d_xyz, &p->d_nodev, &p->d_tile_ref, &p->d_tiles, &p->d_prof2,
                      &p->d_fb_segs, &p->d_fb_recs, &p->d_fb_vals, &p->d_fb_fixes, &p->d_fb_counts};
     for (void** b : bufs)
         if (*b) {
@@ -327,6 +327,7 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
             tiles += p->level_tiles[l];
         }
         if (tiles > 0) HH_TRY(dev_alloc(p, &p->d_tile_ref, sizeof(float) * 16 * (size_t)tiles));
+        if (tiles > 0) HH_TRY(dev_alloc(p, &p->d_tiles, sizeof(hh::DTile) * (size_t)tiles));
     }
     if (p->n_levels > 1) {  // deferred-fallback queue, sized for the widest merge level
         int64_t segs = 1, widest = 1;
@@ -356,6 +357,14 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
     HH_TRY(upload(p->d_nodev, nodev.data(), sizeof(float) * nodev.size(), s));
     HH_TRY(upload(p->d_twiddle, tw.data(), sizeof(float) * tw.size(), s));
+    if (p->d_tiles) {
+        const int te = hh::launch_tile_table(p, cuda_stream);
+        if (te != 0) {
+            free_device(p);
+            delete p;
+            return fail_cuda((cudaError_t)te);
+        }
+    }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         free_device(p);

@@ -60,6 +60,7 @@ struct DTile {
 // Where a launch finds its tiles (see tile_of in the kernels).
 struct TileMap {
     const int64_t* off;    // per-node first tile (n_nodes + 1 entries), or nullptr for the voxel level
+    const DTile* tiles;    // lattice levels: node and origin of every launch tile of the level
     int32_t node0, n_nodes;
     int32_t ntx, nty;      // voxel level: tiles along x and y
 };
@@ -169,6 +170,7 @@ struct hh_plan {
     void* d_need = nullptr;      // uint32[8] bit mask per launch tile of every non-root level (need_base offsets)
     void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
     void* d_tile_ref = nullptr;      // float[16] warm start per launch tile of levels 0..L-2
+    void* d_tiles = nullptr;         // DTile (node, origin) per launch tile of levels 0..L-2 (tile_ref_base)
     std::vector<int64_t> tile_ref_base;  // per level: first tile in d_tile_ref
     // deferred-fallback queue (one merge level at a time)
     void* d_fb_segs = nullptr;
@@ -225,6 +227,7 @@ int launch_adjoint_traversal(const hh_plan* p, const KConst& kc, const void* d_i
 int launch_need_final(const hh_plan* p, const KConst& kc, void* stream);
 int launch_need_level(const hh_plan* p, const KConst& kc, int level, void* stream);
 int launch_tile_refs(const hh_plan* p, const KConst& kc, int level, void* stream);
+int launch_tile_table(const hh_plan* p, void* stream);
 int launch_stage0(const hh_plan* p, const KConst& kc, void* stream);
 int launch_deferred(const hh_plan* p, const KConst& kc, int level, void* out, void* stream);
 int launch_merge(const hh_plan* p, const KConst& kc, int level, void* stream);

@@ -378,6 +378,11 @@ const char* hh_status_string(int status);
 /* Last CUDA error code recorded by the library in this thread (0 = none). */
 int hh_last_cuda_error(void);
 
+/* Diagnostic: kernel launches the library has issued in this process so far (all
+ * threads, every entry point).  The difference across a region counts the library's own
+ * kernels launched there.  No error. */
+long long hh_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

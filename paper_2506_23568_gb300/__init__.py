@@ -127,6 +127,8 @@ def _declare(L):
     L.hh_status_string.argtypes = [ctypes.c_int]
     L.hh_status_string.restype = ctypes.c_char_p
     L.hh_last_cuda_error.argtypes = []
+    L.hh_kernel_launches.argtypes = []
+    L.hh_kernel_launches.restype = ctypes.c_longlong
     L.hh_release_cached_memory.argtypes = []
     for name in SYMBOLS:
         f = getattr(L, name)
@@ -456,6 +458,12 @@ def mip(image, axis=0, out=None, stream=None):
 def release_cached_memory():
     """Free device blocks cached by the library for reuse by later plans."""
     _check(lib().hh_release_cached_memory(), "release_cached_memory")
+
+
+def kernel_launches():
+    """Kernel launches the library has issued in this process (a counter; differences count
+    the launches of a region)."""
+    return int(lib().hh_kernel_launches())
 
 
 def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16, flags=0):

@@ -666,6 +666,7 @@ int launch_need_leaf(const hh_plan* p, const KConst& kc, void* stream) {
     k_need_level<6><<<(unsigned)ntiles, kThreads, 0, as_stream(stream)>>>(
         static_cast<const DNode*>(p->d_nodes), tile_map(p, 0), static_cast<const float*>(p->d_tile_ref), kc,
         zh_mid_of(p), need_of(p, 0), TileMap{}, nullptr, 0, xyz, static_cast<unsigned long long*>(p->d_counters));
+    note_launch();
     return (int)cudaGetLastError();
 }
 
@@ -714,6 +715,7 @@ int launch_adjoint_traversal(const hh_plan* p, const KConst& kc, const void* d_i
         k_adj_init<<<(unsigned)ntiles, kThreads, 0, s>>>(nodes, tile_map(p, level), need_of(p, level),
                                                          static_cast<const float4*>(p->d_xyz) + p->xyz_base[level],
                                                          static_cast<float2*>(p->d_pool[level & 1]));
+        note_launch();
         return (int)cudaGetLastError();
     };
     // final level: the image to the root's children (level L - 2)
@@ -733,6 +735,7 @@ int launch_adjoint_traversal(const hh_plan* p, const KConst& kc, const void* d_i
         } else {
             if (grad) HH_FINAL_ADJ(6, true); else HH_FINAL_ADJ(6, false);
         }
+        note_launch();
 #undef HH_FINAL_ADJ
         if (cudaError_t e = cudaGetLastError()) return (int)e;
     }
@@ -753,6 +756,7 @@ int launch_adjoint_traversal(const hh_plan* p, const KConst& kc, const void* d_i
         } else {
             if (grad) HH_MERGE_ADJ(6, true); else HH_MERGE_ADJ(6, false);
         }
+        note_launch();
 #undef HH_MERGE_ADJ
         if (cudaError_t e = cudaGetLastError()) return (int)e;
     }
@@ -762,12 +766,15 @@ int launch_adjoint_traversal(const hh_plan* p, const KConst& kc, const void* d_i
         if (ntiles > 0) {
             const float2* spool = static_cast<const float2*>(p->d_pool[0]);
             const float4* xyz = static_cast<const float4*>(p->d_xyz) + p->xyz_base[0];
-            if (grad)
+            if (grad) {
                 k_leaf_adj<true><<<(unsigned)ntiles, kThreads, 0, s>>>(nodes, tile_map(p, 0), spool, nodev_of(p, 0),
                                                                        kc, need_of(p, 0), xyz, ao, cnt);
-            else
+                note_launch();
+            } else {
                 k_leaf_adj<false><<<(unsigned)ntiles, kThreads, 0, s>>>(nodes, tile_map(p, 0), spool, nodev_of(p, 0),
                                                                         kc, need_of(p, 0), xyz, ao, cnt);
+                note_launch();
+            }
             if (cudaError_t e = cudaGetLastError()) return (int)e;
         }
     }

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -240,6 +241,10 @@ int upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 
 namespace hh {
 int note_cuda_error(int cuda_error) { return fail_cuda((cudaError_t)cuda_error); }
+
+// Kernel launches issued by the library since the process started (every launch site calls it).
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace hh
 
 extern "C" {
@@ -898,5 +903,7 @@ const char* hh_status_string(int status) {
 }
 
 int hh_last_cuda_error(void) { return g_last_cuda; }
+
+long long hh_kernel_launches(void) { return hh::g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -238,6 +238,8 @@ int launch_preimage_probe(const hh_plan* p, const KConst& kc, int node, const do
                           void* stream);
 KConst make_kconst(const hh_plan* p);
 
+// hh_api.cpp: count one kernel launch of the library (hh_kernel_launches)
+void note_launch();
 // hh_api.cpp: record a CUDA error for hh_last_cuda_error() and map it to a status
 int note_cuda_error(int cuda_error);
 // hh_api.cpp: range constants and a range gate covering every (voxel, position) distance

@@ -113,6 +113,7 @@ extern "C" int bpa_form_image_noalloc(const double* traj_xyz, int64_t n_pos, con
     e = cudaMemcpyAsync(d_traj, traj_xyz, sizeof(double) * 3 * (size_t)n_pos, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return hh::note_cuda_error((int)e);
     k_noalloc_twiddles<<<(unsigned)((2 * tmp.n_fft + 255) / 256), 256, 0, s>>>(d_tw, tmp.n_fft);
+    hh::note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return hh::note_cuda_error((int)e);
     e = (cudaError_t)hh::launch_rc(echo_c64, nullptr, n_pos, n_f, tmp.n_fft, tmp.gate0, tmp.gate_n, d_tw, d_prof,

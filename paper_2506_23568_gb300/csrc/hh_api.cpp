@@ -203,8 +203,11 @@ void member_arrays(const hh_plan* p, const std::vector<hh::DNode>& dn, std::vect
                    std::vector<float>& nodev) {
     const int64_t n_pos = p->n_pos;
     mem_pos.assign(3 * (size_t)n_pos, 0.0);
-    for (int64_t q = 0; q < n_pos; ++q)
-        for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
+    const int64_t blk = 4096;  // positions in tree order, gathered in blocks
+    hh::parallel_for((n_pos + blk - 1) / blk, n_pos >= 32768 ? 16 : 1, [&](int64_t b) {
+        for (int64_t q = b * blk; q < std::min(n_pos, (b + 1) * blk); ++q)
+            for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
+    });
     const int n_vec_levels = std::max(1, p->n_levels - 1);
     nodev.assign(4 * (size_t)n_pos * (size_t)n_vec_levels, 0.f);
     const int64_t n_vec_nodes = p->n_levels > 1 ? p->level_start[p->n_levels - 1] : 0;

@@ -2,9 +2,12 @@
 // grids, range gate, launch tiles and interpolation weights (Sec. III, Sec. IV-A).
 // FP64 throughout; nothing here touches the GPU.
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -243,13 +246,23 @@ int validate_inputs(const double* traj, int64_t n_pos, const double* freqs, int3
 }
 
 std::vector<float> twiddle_table(int n_fft) {
-    // W[q] = exp(+j pi q / n_fft), q in [0, 2 n_fft)
+    // W[q] = exp(+j pi q / n_fft), q in [0, 2 n_fft); computed once per size and kept
+    // (every plan of a scan series uses the same transform length)
+    static std::mutex mu;
+    static std::vector<std::pair<int, std::vector<float>>> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const auto& e : cache)
+            if (e.first == n_fft) return e.second;
+    }
     std::vector<float> t(4 * (size_t)n_fft);
     for (int q = 0; q < 2 * n_fft; ++q) {
         double ang = kPi * (double)q / (double)n_fft;
         t[2 * q] = (float)std::cos(ang);
         t[2 * q + 1] = (float)std::sin(ang);
     }
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() < 16) cache.emplace_back(n_fft, t);
     return t;
 }
 
@@ -318,6 +331,89 @@ WPoly weight_poly(int taps, double eta) {
     return wp;
 }
 
+namespace {
+
+// Host workers kept for the life of the process, so that the planner's parallel loops
+// (a few per plan, each well under a millisecond of work) do not pay for creating
+// threads.  One loop runs at a time; a call that finds the workers busy (another host
+// thread, or a loop inside a loop) runs on threads of its own instead.
+class WorkerPool {
+  public:
+    explicit WorkerPool(int n) {
+        for (int i = 0; i < n; ++i) workers_.emplace_back([this]() { work(); });
+    }
+    ~WorkerPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& w : workers_) w.join();
+    }
+    int size() const { return (int)workers_.size(); }
+    // Runs f(i) for i in [0, n) on the calling thread and up to `helpers` workers; false
+    // (nothing run) when the pool is in use.
+    bool run(int64_t n, int helpers, const std::function<void(int64_t)>& f) {
+        std::unique_lock<std::mutex> busy(call_mu_, std::try_to_lock);
+        if (!busy.owns_lock()) return false;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            job_ = &f;
+            n_ = n;
+            next_.store(0);
+            want_ = helpers;
+            pending_ = 0;
+            ++gen_;
+        }
+        cv_.notify_all();
+        drain(f, n);
+        std::unique_lock<std::mutex> lk(mu_);
+        want_ = 0;  // late workers of this generation take nothing
+        done_cv_.wait(lk, [this]() { return pending_ == 0; });
+        job_ = nullptr;
+        return true;
+    }
+
+  private:
+    void drain(const std::function<void(int64_t)>& f, int64_t n) {
+        for (int64_t i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) f(i);
+    }
+    void work() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&]() { return stop_ || gen_ != seen; });
+            if (stop_) return;
+            seen = gen_;
+            if (want_ <= 0 || job_ == nullptr) continue;
+            --want_;
+            ++pending_;
+            const std::function<void(int64_t)>* f = job_;
+            const int64_t n = n_;
+            lk.unlock();
+            drain(*f, n);
+            lk.lock();
+            if (--pending_ == 0) done_cv_.notify_all();
+        }
+    }
+    std::vector<std::thread> workers_;
+    std::mutex mu_, call_mu_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int64_t)>* job_ = nullptr;
+    int64_t n_ = 0;
+    std::atomic<int64_t> next_{0};
+    int want_ = 0, pending_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+WorkerPool& worker_pool() {
+    static WorkerPool pool(std::max(0, std::min(31, (int)std::thread::hardware_concurrency() - 1)));
+    return pool;
+}
+
+}  // namespace
+
 void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& f) {
     const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
     const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)threads, n}));
@@ -325,6 +421,8 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& f)
         for (int64_t i = 0; i < n; ++i) f(i);
         return;
     }
+    WorkerPool& wp = worker_pool();
+    if (wp.size() > 0 && wp.run(n, (int)std::min<int64_t>(nt - 1, wp.size()), f)) return;
     std::vector<std::thread> pool;
     for (int64_t t = 1; t < nt; ++t)
         pool.emplace_back([&f, n, nt, t]() {
@@ -467,16 +565,7 @@ int build_host_plan(hh_plan* p) {
         }
     };
     // nodes are independent: spread them over the host threads (same results in any split)
-    {
-        const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
-        const int64_t nt = std::min<int64_t>(std::min<int64_t>(hw, 32), std::max<int64_t>(1, n_lattice_nodes / 8));
-        std::vector<std::thread> pool;
-        for (int64_t t = 0; t < nt; ++t)
-            pool.emplace_back([&, t]() {
-                for (int64_t k = t; k < n_lattice_nodes; k += nt) lattice_of(k);
-            });
-        for (auto& th : pool) th.join();
-    }
+    parallel_for(n_lattice_nodes, n_lattice_nodes >= 8 ? 32 : 1, lattice_of);
     p->level_samples.assign(p->n_levels, 0);
     p->max_pool = 0;
     for (int l = 0; l + 1 < p->n_levels; ++l) {

@@ -55,11 +55,12 @@ PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
               "hardware": "one core of a 4.5 GHz Ryzen 9 7950X, C++ without parallelisation"}
 
 # DRAM bytes (read + write) per evaluated sample of a stage's kernel, from an ncu capture of
-# one launch on the mid workload (dram__bytes_read.sum + dram__bytes_write.sum = 54.4 MB +
-# 120.5 MB for 10,076,991 evaluated leaf samples; profiles/k_stage0_k_merge_mid.md), scaled to
-# a launch by the samples it evaluates; keyed by the kernel revision, null for other kernels.
-TRAFFIC_PER_SAMPLE = {("leaf_subimages", "two-sample loop, TMA windows"): 174.9e6 / 10076991}
-STAGE0_REVISION = "two-sample loop, TMA windows"
+# one launch on the mid workload in its benchmark plan (dram__bytes_read.sum +
+# dram__bytes_write.sum = 51.2 MB + 79.0 MB for 7,371,281 evaluated leaf samples;
+# profiles/k_stage0_mid.md), scaled to a launch by the samples it evaluates; keyed by the
+# kernel revision, null for other kernels.
+TRAFFIC_PER_SAMPLE = {("leaf_subimages", "paired two-sample loop, tile table"): (51223552 + 78989312) / 7371281}
+STAGE0_REVISION = "paired two-sample loop, tile table"
 
 # Algorithmic work per unit: a BPA-type update (one position at one point) takes one
 # rsqrt and one sincos (3 MUFU results) and about 25 FP32 operations

@@ -128,7 +128,7 @@ int dev_alloc(hh_plan* p, void** ptr, size_t bytes) {
 void free_device(hh_plan* p) {
     void** bufs[] = {&p->d_tile_off, &p->d_nodes, &p->d_mem_pos, &p->d_perm, &p->d_prof, &p->d_pool[0], &p->d_pool[1],
                      &p->d_twiddle, &p->d_counters, &p->d_echo_stage, &p->d_image_stage,
-                     &p->d_need, &p->d_xyz, &p->d_nodev, &p->d_tile_ref, &p->d_tiles, &p->d_prof2,
+                     &p->d_need, &p->d_xyz, &p->d_nodev, &p->d_tile_ref, &p->d_tiles, &p->d_pair_off, &p->d_pairs, &p->d_prof2,
                      &p->d_fb_segs, &p->d_fb_recs, &p->d_fb_vals, &p->d_fb_fixes, &p->d_fb_counts};
     for (void** b : bufs)
         if (*b) {
@@ -336,6 +336,16 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         }
         if (tiles > 0) HH_TRY(dev_alloc(p, &p->d_tile_ref, sizeof(float) * 16 * (size_t)tiles));
         if (tiles > 0) HH_TRY(dev_alloc(p, &p->d_tiles, sizeof(hh::DTile) * (size_t)tiles));
+        p->pair_base.assign(p->n_levels, 0);
+        int64_t pairs = 0;
+        for (int l = 0; l + 1 < p->n_levels; ++l) {
+            p->pair_base[l] = pairs;
+            pairs += p->level_pairs[l];
+        }
+        if (pairs > 0) {
+            HH_TRY(dev_alloc(p, &p->d_pairs, 8 * (size_t)pairs));
+            HH_TRY(dev_alloc(p, &p->d_pair_off, sizeof(int64_t) * p->pair_off.size()));
+        }
     }
     if (p->n_levels > 1) {  // deferred-fallback queue, sized for the widest merge level
         int64_t segs = 1, widest = 1;
@@ -361,6 +371,8 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
     HH_TRY(upload(p->d_nodes, dn.data(), sizeof(hh::DNode) * dn.size(), s));
     if (!p->tile_off.empty())
         HH_TRY(upload(p->d_tile_off, p->tile_off.data(), sizeof(int64_t) * p->tile_off.size(), s));
+    if (p->d_pair_off)
+        HH_TRY(upload(p->d_pair_off, p->pair_off.data(), sizeof(int64_t) * p->pair_off.size(), s));
     HH_TRY(upload(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), s));
     HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
     HH_TRY(upload(p->d_nodev, nodev.data(), sizeof(float) * nodev.size(), s));

@@ -152,6 +152,9 @@ struct hh_plan {
     std::vector<int64_t> level_tiles;        // launch tiles per level (root: voxel tiles)
     std::vector<int64_t> tile_off;           // per-node first tile, all non-root levels concatenated
     std::vector<int64_t> tile_off_base;      // per level: first entry in tile_off
+    std::vector<int64_t> level_pairs;        // merge launches: tile pairs per level (see pair_off)
+    std::vector<int64_t> pair_off;           // per-node first tile pair, all non-root levels concatenated
+    std::vector<int64_t> pair_off_base;      // per level: first entry in pair_off
     hh::WPoly wpoly{};                       // interpolation weights (polynomials)
     int64_t max_pool = 0;
     // device state
@@ -171,6 +174,9 @@ struct hh_plan {
     void* d_xyz = nullptr;       // float4 preimage (node frame, w = feasible) per sample of levels 1..L-2
     void* d_tile_ref = nullptr;      // float[16] warm start per launch tile of levels 0..L-2
     void* d_tiles = nullptr;         // DTile (node, origin) per launch tile of levels 0..L-2 (tile_ref_base)
+    void* d_pair_off = nullptr;      // int64 copy of pair_off
+    void* d_pairs = nullptr;         // int2 (tile, tile or -1) per tile pair of levels 0..L-2 (pair_base)
+    std::vector<int64_t> pair_base;  // per level: first pair in d_pairs
     std::vector<int64_t> tile_ref_base;  // per level: first tile in d_tile_ref
     // deferred-fallback queue (one merge level at a time)
     void* d_fb_segs = nullptr;

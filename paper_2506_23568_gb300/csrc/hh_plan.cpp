@@ -646,6 +646,23 @@ int build_host_plan(hh_plan* p) {
         p->tile_off.push_back(t);
         p->level_tiles[l] = t;
     }
+    // tile pairs of the merge launches: two launch tiles adjacent along n in one (u, v)
+    // column of a node (the last tile of a column alone when the column has an odd count)
+    p->level_pairs.assign(p->n_levels, 0);
+    p->pair_off.clear();
+    p->pair_off_base.assign(p->n_levels, 0);
+    for (int l = 0; l + 1 < p->n_levels; ++l) {
+        p->pair_off_base[l] = (int64_t)p->pair_off.size();
+        int64_t t = 0;
+        for (int64_t k = p->level_start[l]; k < p->level_start[l + 1]; ++k) {
+            const HNode& nd = p->nodes[k];
+            p->pair_off.push_back(t);
+            const int64_t nt2 = (nd.N[2] + kTile2 - 1) / kTile2;
+            t += ((nd.N[0] + kTile0 - 1) / kTile0) * ((nd.N[1] + kTile1 - 1) / kTile1) * ((nt2 + 1) / 2);
+        }
+        p->pair_off.push_back(t);
+        p->level_pairs[l] = t;
+    }
     {
         const hh_grid& g = p->grid;
         p->level_tiles[p->n_levels - 1] = (int64_t)((g.nx + kTile0 - 1) / kTile0) * ((g.ny + kTile1 - 1) / kTile1) *

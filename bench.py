@@ -40,12 +40,12 @@ WORKLOADS = {
             "0.175 m pitch centred 0.4 m deep, 101x101x51 grid over 0.5 m^3",
 }
 # Plan per workload: the autotuner's choice (paper_2506_23568_gb300.tune: the Sec. IV-B
-# operation count ranks the candidates, the cheapest are timed, acceptance at NRMSE <= -32 dB
-# against direct BPA over every 8th z-slab).  Large: leaf 256, eta 1.5, 6 taps (-33.1 dB,
-# 63.4 ms plan + image in the sweep; eta 1.6: -36.9 dB, 69.7 ms; no 4-tap plan reached
-# -32 dB at a lower cost).  Mid: leaf 512, eta 1.5 (-34.9 dB, 17.4 ms; leaf 256 eta 1.6:
-# -38.4 dB, 21.1 ms).
-PLAN_CFG = {"large": dict(leaf_size=256, eta=1.5), "mid": dict(leaf_size=512, eta=1.5),
+# operation count ranks the candidates, every candidate of a 16-point grid is timed, acceptance
+# at NRMSE <= -32 dB against direct BPA over every 8th z-slab).  Large: leaf 1024, eta 1.5,
+# 6 taps (-34.1 dB, 51.1 ms plan + image in the sweep; leaf 256 eta 1.5: -33.1 dB, 52.0 ms;
+# eta 1.4 misses the bar; no 4-tap plan reached -32 dB at a lower cost).  Mid: leaf 1024,
+# eta 1.5 (-36.1 dB, 15.6 ms; leaf 512 eta 1.5: -34.9 dB, 16.1 ms).
+PLAN_CFG = {"large": dict(leaf_size=1024, eta=1.5), "mid": dict(leaf_size=1024, eta=1.5),
             "tiny": dict(leaf_size=32), "sim1": dict(leaf_size=32)}
 # the paper's Table II (Sim I, one CPU core; BPA / HHFFBPA), quoted as context only
 PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
@@ -55,11 +55,11 @@ PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
               "hardware": "one core of a 4.5 GHz Ryzen 9 7950X, C++ without parallelisation"}
 
 # DRAM bytes (read + write) per evaluated sample of a stage's kernel, from an ncu capture of
-# one launch on the mid workload in its benchmark plan (dram__bytes_read.sum +
-# dram__bytes_write.sum = 51.2 MB + 79.0 MB for 7,371,281 evaluated leaf samples;
-# profiles/k_stage0_mid.md), scaled to a launch by the samples it evaluates; keyed by the
-# kernel revision, null for other kernels.
-TRAFFIC_PER_SAMPLE = {("leaf_subimages", "paired two-sample loop, tile table"): (51223552 + 78989312) / 7371281}
+# one launch on the mid workload in its benchmark plan (leaf 1024, eta 1.5: the large
+# workload's leaf size; dram__bytes_read.sum + dram__bytes_write.sum = 44.8 MB + 49.8 MB for
+# 5,713,647 evaluated leaf samples; profiles/k_stage0_mid.md), scaled to a launch by the
+# samples it evaluates; keyed by the kernel revision, null for other kernels.
+TRAFFIC_PER_SAMPLE = {("leaf_subimages", "paired two-sample loop, tile table"): (44828928 + 49848832) / 5713647}
 STAGE0_REVISION = "paired two-sample loop, tile table"
 
 # Algorithmic work per unit: a BPA-type update (one position at one point) takes one

@@ -178,14 +178,15 @@ def test_mid_sampled_parity(hh):
     assert oracle.nrmse_db(img.cpu().numpy(), bimg.cpu().numpy()) < -30
 
 
-def test_large_sampled_parity_benchmark_plan(hh):
-    """Full-size large workload in the benchmark's launch configuration and plan (leaf 256,
-    eta 1.5, 6 taps): voxel clusters at the centre, an edge and a corner of the grid against
-    the oracle (demand-driven), a subset against the oracle's BPA-RC, and the whole volume
-    against the GPU's direct BPA (-30 dB)."""
+@pytest.mark.parametrize("leaf", [1024, 256])
+def test_large_sampled_parity_benchmark_plan(hh, leaf):
+    """Full-size large workload in the benchmark's launch configuration and plan (leaf 1024,
+    eta 1.5, 6 taps: four levels) and with leaf 256 (five levels): voxel clusters at the
+    centre, an edge and a corner of the grid against the oracle (demand-driven), a subset
+    against the oracle's BPA-RC, and the whole volume against the GPU's direct BPA (-30 dB)."""
     s, e = _scene("large")
     g = s.grid
-    cfg = dict(leaf_size=256, eta=1.5)
+    cfg = dict(leaf_size=leaf, eta=1.5)
     plan = hh.Plan(s.traj, s.freqs, g, **cfg)
     img = plan.form_image(e)
     cnt = plan.counters()

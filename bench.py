@@ -60,7 +60,7 @@ PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
 # 5,713,647 evaluated leaf samples; profiles/k_stage0_mid.md), scaled to a launch by the
 # samples it evaluates; keyed by the kernel revision, null for other kernels.
 TRAFFIC_PER_SAMPLE = {("leaf_subimages", "paired two-sample loop, tile table"): (44828928 + 49848832) / 5713647}
-STAGE0_REVISION = "paired two-sample loop, tile table"
+STAGE0_REVISION = "paired two-sample loop, tile table, floor(256/npair) member groups"
 
 # Algorithmic work per unit: a BPA-type update (one position at one point) takes one
 # rsqrt and one sincos (3 MUFU results) and about 25 FP32 operations
@@ -179,8 +179,8 @@ def roofline_of(kind, ms, units, peaks, clk_mhz):
     """(achieved, peak, unit, bound, frac) for a kernel from its algorithmic work."""
     f = clk_mhz * 1e6
     sms = sm_count()
-    if kind == "mufu":  # units = MUFU operations
-        peak = MUFU_PER_SM_CLK * sms * f
+    if kind == "mufu":  # units = MUFU operations; the measured rate where there is one
+        peak = peaks.get("mufu_tps") or MUFU_PER_SM_CLK * sms * f
         ach = units / (ms * 1e-3)
         return ach / 1e12, peak / 1e12, "TMUFU/s", "alu", ach / peak
     if kind == "fp32":  # units = FLOP
@@ -271,6 +271,9 @@ def run_gpu(args):
     for _ in range(args.warmup):
         plan, _ = step(False)
         plan.close()
+    # the MUFU rate of this device, measured (one rsqrt feeding one sine and one cosine per
+    # step, as in an update), before the timed region: the denominator of the MUFU rooflines
+    peaks["mufu_tps"] = hh.mufu_throughput("update_mix", 4096)[0]
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -319,7 +322,7 @@ def run_gpu(args):
     roof_ms = 0.0
     for w in work:
         t_fp = w["flop"] / (FP32_PER_SM_CLK * sm_count() * f)
-        t_mu = w["mufu"] / (MUFU_PER_SM_CLK * sm_count() * f)
+        t_mu = w["mufu"] / (peaks.get("mufu_tps") or MUFU_PER_SM_CLK * sm_count() * f)
         t_hb = w["bytes"] / (peaks["hbm_gbs"] * 1e9)
         w["roof_ms"] = 1e3 * max(t_fp, t_mu, t_hb)
         w["bound"] = ["fp32", "mufu", "hbm"][int(np.argmax([t_fp, t_mu, t_hb]))]
@@ -332,6 +335,7 @@ def run_gpu(args):
     kind = dom["bound"]
     units = {"fp32": dom["flop"], "mufu": dom["mufu"], "hbm": dom["bytes"]}[kind]
     d_ach, d_peak, d_unit, d_bound, d_frac = roofline_of(kind, dom["ms"], units, peaks, clk_mhz)
+    d_kind_mufu = kind == "mufu"
 
     # position gradient of direct BPA on the differentiation scene (8,192 positions, 128 freqs,
     # 128x128x32 grid, echoes from a track with smooth 1 mm offsets): CUDA events around the call
@@ -418,8 +422,13 @@ def run_gpu(args):
                                  if (dom["stage"], STAGE0_REVISION) in TRAFFIC_PER_SAMPLE else None),
                      "traffic_source": "ncu dram bytes of one launch on the mid workload, scaled by the "
                                        "evaluated samples",
-                     "peak_source": f'{peaks["source"]} ({MUFU_PER_SM_CLK:g} SFU/clk/SM, {FP32_PER_SM_CLK:g} '
-                                    f'FLOP/clk/SM x {sm_count()} SMs at the sampled {clk_mhz:.0f} MHz)'},
+                     "peak_source": (f'measured: MUFU probe hh_mufu_throughput (rsqrt feeding sin and cos, '
+                                     f'2048 threads/SM), {peaks["mufu_tps"] / 1e12:.3f} T/s = '
+                                     f'{peaks["mufu_tps"] / (sm_count() * clk_mhz * 1e6):.2f} results/clk/SM at '
+                                     f'the sampled {clk_mhz:.0f} MHz (nominal {MUFU_PER_SM_CLK:g})'
+                                     if d_kind_mufu else
+                                     f'derived ({FP32_PER_SM_CLK:g} FLOP/clk/SM x {sm_count()} SMs at the '
+                                     f'sampled {clk_mhz:.0f} MHz)')},
         "plan_ms": statistics.mean(t_plan),
         "roofline_pipeline": {"roofline_ms": roof_ms, "kernels_ms": hh_kernel_ms,
                               "frac": roof_ms / hh_kernel_ms if hh_kernel_ms else None,

@@ -378,6 +378,26 @@ const char* hh_status_string(int status);
 /* Last CUDA error code recorded by the library in this thread (0 = none). */
 int hh_last_cuda_error(void);
 
+/*
+ * hh_mufu_throughput -- measure the special-function unit's rate on the current device
+ * for the approximate functions of the backprojection update (Eq. 3: one reciprocal
+ * square root for the range, one sine and one cosine for the carrier phase), the bound
+ * of every kernel that sums (sample, position) updates.
+ *   op        HH_MUFU_RSQRT, HH_MUFU_SIN, HH_MUFU_COS, or HH_MUFU_UPDATE_MIX (one
+ *             rsqrt feeding one sine and one cosine, three results per step).
+ *   iters     steps per dependency chain (1 .. 2^20); the grid holds 2048 threads per
+ *             SM with eight chains each.  iters = 4096 takes about 2 ms.
+ *   mufu_ops  out: MUFU results computed by the timed launch.
+ *   ms        out: its duration (CUDA events on cuda_stream, after one untimed launch).
+ * Synchronises the stream.  Errors: HH_ERR_ARG (null outputs, op or iters out of range),
+ * HH_ERR_CUDA.
+ */
+#define HH_MUFU_RSQRT 0
+#define HH_MUFU_SIN 1
+#define HH_MUFU_COS 2
+#define HH_MUFU_UPDATE_MIX 3
+int hh_mufu_throughput(int32_t op, int32_t iters, void* cuda_stream, int64_t* mufu_ops, float* ms);
+
 /* Diagnostic: kernel launches the library has issued in this process so far (all
  * threads, every entry point).  The difference across a region counts the library's own
  * kernels launched there.  No error. */

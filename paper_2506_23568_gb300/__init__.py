@@ -34,6 +34,7 @@ HH_ERR_HOST_ONLY = 8
 HH_ERR_SCRATCH_LIMIT = 9
 HH_FLAG_HOST_ONLY = 1
 HH_FLAG_FP32_REFS = 2
+MUFU_OPS = {"rsqrt": 0, "sin": 1, "cos": 2, "update_mix": 3}
 
 # every symbol declared in include/hhffbp.h
 SYMBOLS = ["hhffbp_default_config", "hhffbp_interp_weights", "hhffbp_plan", "hhffbp_plan_destroy", "hhffbp_plan_info", "hhffbp_plan_export",
@@ -44,7 +45,7 @@ SYMBOLS = ["hhffbp_default_config", "hhffbp_interp_weights", "hhffbp_plan", "hhf
            "hhffbp_batch_create", "hhffbp_batch_form_images", "hhffbp_batch_destroy",
            "hh_status_string",
            "hh_last_cuda_error",
-           "hh_release_cached_memory"]
+           "hh_release_cached_memory", "hh_kernel_launches", "hh_mufu_throughput"]
 STAGE_NAMES = {0: "range_compression", 1: "need_final", 2: "need_level", 3: "leaf_subimages", 4: "merge",
                5: "final", 6: "h2d", 7: "d2h"}
 
@@ -129,6 +130,7 @@ def _declare(L):
     L.hh_last_cuda_error.argtypes = []
     L.hh_kernel_launches.argtypes = []
     L.hh_kernel_launches.restype = ctypes.c_longlong
+    L.hh_mufu_throughput.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, i64p, ctypes.POINTER(ctypes.c_float)]
     L.hh_release_cached_memory.argtypes = []
     for name in SYMBOLS:
         f = getattr(L, name)
@@ -464,6 +466,16 @@ def kernel_launches():
     """Kernel launches the library has issued in this process (a counter; differences count
     the launches of a region)."""
     return int(lib().hh_kernel_launches())
+
+
+def mufu_throughput(op="update_mix", iters=4096, stream=None):
+    """Measured special-function-unit rate on the current device: (MUFU results per
+    second, results, milliseconds) of one timed probe launch.  op: 'rsqrt', 'sin', 'cos' or
+    'update_mix' (one rsqrt feeding one sine and one cosine, as in a backprojection update)."""
+    ops, ms = ctypes.c_int64(0), ctypes.c_float(0)
+    _check(lib().hh_mufu_throughput(MUFU_OPS[op], int(iters), _stream_ptr(stream), ctypes.byref(ops),
+                                    ctypes.byref(ms)), "mufu_throughput")
+    return ops.value / (ms.value * 1e-3), ops.value, ms.value
 
 
 def bpa_form_image(traj, freqs, grid, echo, out=None, stream=None, range_os=16, flags=0):

@@ -2,6 +2,7 @@
 // grids, range gate, launch tiles and interpolation weights (Sec. III, Sec. IV-A).
 // FP64 throughout; nothing here touches the GPU.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <condition_variable>
 #include <cmath>
@@ -364,6 +365,7 @@ class WorkerPool {
             want_ = helpers;
             pending_ = 0;
             ++gen_;
+            gen_pub_.store(gen_, std::memory_order_release);
         }
         cv_.notify_all();
         drain(f, n);
@@ -378,10 +380,15 @@ class WorkerPool {
     void drain(const std::function<void(int64_t)>& f, int64_t n) {
         for (int64_t i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) f(i);
     }
+    // A worker polls for the next job for a short while before it sleeps: the plan's
+    // parallel loops follow one another within microseconds, and a wake-up through the
+    // condition variable costs tens of microseconds per loop.
     void work() {
         uint64_t seen = 0;
-        std::unique_lock<std::mutex> lk(mu_);
         for (;;) {
+            for (int i = 0; i < kPollIters && gen_pub_.load(std::memory_order_acquire) == seen; ++i) {
+            }
+            std::unique_lock<std::mutex> lk(mu_);
             cv_.wait(lk, [&]() { return stop_ || gen_ != seen; });
             if (stop_) return;
             seen = gen_;
@@ -396,7 +403,9 @@ class WorkerPool {
             if (--pending_ == 0) done_cv_.notify_all();
         }
     }
+    static constexpr int kPollIters = 1 << 18;
     std::vector<std::thread> workers_;
+    std::atomic<uint64_t> gen_pub_{0};
     std::mutex mu_, call_mu_;
     std::condition_variable cv_, done_cv_;
     const std::function<void(int64_t)>* job_ = nullptr;
@@ -430,6 +439,69 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& f)
         });
     for (int64_t i = 0; i < n; i += nt) f(i);
     for (auto& th : pool) th.join();
+}
+
+// Moves the `need` smallest members of idx[0, n) in (coordinate along `axis`, index)
+// order to the front and the rest behind them (order within each part as found).  The
+// coordinates are binned by a monotone map onto equal-width buckets between their minimum
+// and maximum, so that every bucket below the one holding the boundary lies wholly in
+// front and every bucket above it wholly behind; only that bucket is ordered exactly.
+// Linear time; the partition equals that of a full sort.
+void select_lower(const double* T, int axis, int64_t* idx, int64_t n, int64_t need) {
+    auto less = [T, axis](int64_t u, int64_t v) {
+        const double cu = T[3 * u + axis], cv = T[3 * v + axis];
+        return cu < cv || (cu == cv && u < v);
+    };
+    if (need <= 0 || need >= n) return;
+    constexpr int kBins = 4096;
+    if (n < 4 * kBins / 16) {
+        std::nth_element(idx, idx + need, idx + n, less);
+        return;
+    }
+    double lo4[4] = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi4[4] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+    for (int64_t q = 0; q < n; ++q) {  // four independent chains
+        const double x = T[3 * idx[q] + axis];
+        lo4[q & 3] = x < lo4[q & 3] ? x : lo4[q & 3];
+        hi4[q & 3] = x > hi4[q & 3] ? x : hi4[q & 3];
+    }
+    const double lo = std::min(std::min(lo4[0], lo4[1]), std::min(lo4[2], lo4[3]));
+    const double hi = std::max(std::max(hi4[0], hi4[1]), std::max(hi4[2], hi4[3]));
+    const double scale = (double)kBins / (hi - lo);
+    if (!(hi > lo) || !std::isfinite(scale)) {
+        std::nth_element(idx, idx + need, idx + n, less);
+        return;
+    }
+    thread_local std::vector<uint16_t> bin;
+    thread_local std::vector<int64_t> out, cand;
+    bin.resize(n);
+    out.resize(n + 1);  // the branch-free partition below writes one slot past each part
+    int64_t count[kBins] = {0};
+    for (int64_t q = 0; q < n; ++q) {
+        const int b = std::min(kBins - 1, (int)((T[3 * idx[q] + axis] - lo) * scale));
+        bin[q] = (uint16_t)b;
+        ++count[b];
+    }
+    int kb = 0;
+    int64_t below = 0;
+    while (below + count[kb] < need) below += count[kb++];
+    cand.resize(count[kb] + 1);
+    int64_t L = 0, R = need, C = 0;
+    int64_t* o = out.data();
+    int64_t* c = cand.data();
+    for (int64_t q = 0; q < n; ++q) {  // every member is written to all three parts; only its own advances
+        const int64_t id = idx[q];
+        const int b = bin[q];
+        o[L] = id;
+        o[R] = id;
+        c[C] = id;
+        L += b < kb;
+        R += b > kb;
+        C += b == kb;
+    }
+    const int64_t take = need - below;
+    std::nth_element(c, c + take, c + C, less);
+    for (int64_t i = 0; i < C; ++i) o[i < take ? L++ : R++] = c[i];
+    std::copy(out.begin(), out.begin() + n, idx);
 }
 
 int build_host_plan(hh_plan* p) {
@@ -468,29 +540,16 @@ int build_host_plan(hh_plan* p) {
         }
         nb.push_back(n);
     }
-    // the selections: node j of depth d splits at its mid point; the two halves are
-    // independent, so subtrees below depth kSplitSpawn run on their own host threads
-    // (every range sees the same sequence of operations whichever thread runs it)
-    constexpr int kSplitSpawn = 4;
-    std::function<void(int, size_t)> split = [&](int d, size_t j) {
-        if (d >= D) return;
-        const int axis = d & 1;
-        const int64_t b0 = bounds[d][j], b1 = bounds[d][j + 1], mid = b0 + (b1 - b0) / 2;
-        auto less = [&](int64_t u, int64_t v) {
-            double cu = T[3 * u + axis], cv = T[3 * v + axis];
-            return cu < cv || (cu == cv && u < v);
-        };
-        std::nth_element(p->perm.begin() + b0, p->perm.begin() + mid, p->perm.begin() + b1, less);
-        if (d < kSplitSpawn && b1 - b0 >= 4096) {
-            std::thread left([&split, d, j]() { split(d + 1, 2 * j); });
-            split(d + 1, 2 * j + 1);
-            left.join();
-        } else {
-            split(d + 1, 2 * j);
-            split(d + 1, 2 * j + 1);
-        }
-    };
-    split(0, 0);
+    // the selections: node j of depth d splits at its mid point.  The nodes of one depth
+    // are independent and run on the host workers; each range sees the same operations
+    // whichever thread runs it.
+    for (int d = 0; d < D; ++d) {
+        const int64_t cnt = (int64_t)1 << d;
+        parallel_for(cnt, cnt >= 2 ? 16 : 1, [&](int64_t j) {
+            const int64_t b0 = bounds[d][j], b1 = bounds[d][j + 1];
+            select_lower(T, d & 1, p->perm.data() + b0, b1 - b0, (b1 - b0) / 2);
+        });
+    }
     // materialised depths: D, D - s, ..., (> 0), then the root
     const int step = cfg.merge_factor == 4 ? 2 : 1;
     std::vector<int> depths;
@@ -520,26 +579,46 @@ int build_host_plan(hh_plan* p) {
         }
     }
     p->level_start[p->n_levels] = (int64_t)p->nodes.size();
-    // member boxes and mean heights, one node per task
-    parallel_for((int64_t)p->nodes.size(), n >= 32768 ? 16 : 1, [&](int64_t k) {
-        HNode& nd = p->nodes[k];
-        double a = HUGE_VAL, b = -HUGE_VAL, e = HUGE_VAL, g = -HUGE_VAL;
-        double zs = 0;
-        nd.zmin = HUGE_VAL;
-        nd.zmax = -HUGE_VAL;
+    // member boxes and height sums: the leaves from their members (one leaf per task), every
+    // other node as the union of its children's (the same minima and maxima)
+    std::vector<std::array<double, 7>> raw(p->nodes.size());  // x min, x max, y min, y max, z min, z max, z sum
+    parallel_for(p->level_start[1] - p->level_start[0], n >= 32768 ? 16 : 1, [&](int64_t k) {
+        const HNode& nd = p->nodes[k];
+        std::array<double, 7> r = {HUGE_VAL, -HUGE_VAL, HUGE_VAL, -HUGE_VAL, HUGE_VAL, -HUGE_VAL, 0.0};
         for (int64_t q = nd.begin; q < nd.end; ++q) {
             const double* pp = T + 3 * p->perm[q];
-            a = std::min(a, pp[0]); b = std::max(b, pp[0]);
-            e = std::min(e, pp[1]); g = std::max(g, pp[1]);
-            nd.zmin = std::min(nd.zmin, pp[2]);
-            nd.zmax = std::max(nd.zmax, pp[2]);
-            zs += pp[2];
+            r[0] = std::min(r[0], pp[0]); r[1] = std::max(r[1], pp[0]);
+            r[2] = std::min(r[2], pp[1]); r[3] = std::max(r[3], pp[1]);
+            r[4] = std::min(r[4], pp[2]); r[5] = std::max(r[5], pp[2]);
+            r[6] += pp[2];
         }
-        nd.zbar = zs / (double)(nd.end - nd.begin);
+        raw[k] = r;
+    });
+    for (int l = 1; l < p->n_levels; ++l)
+        for (int64_t k = p->level_start[l]; k < p->level_start[l + 1]; ++k) {
+            const HNode& nd = p->nodes[k];
+            std::array<double, 7> r = raw[nd.child0];
+            for (int64_t c = 1; c < nd.nchild; ++c) {
+                const std::array<double, 7>& o = raw[nd.child0 + c];
+                for (int i = 0; i < 6; i += 2) {
+                    r[i] = std::min(r[i], o[i]);
+                    r[i + 1] = std::max(r[i + 1], o[i + 1]);
+                }
+                r[6] += o[6];
+            }
+            raw[k] = r;
+        }
+    for (size_t k = 0; k < p->nodes.size(); ++k) {
+        HNode& nd = p->nodes[k];
+        const std::array<double, 7>& r = raw[k];
+        double a = r[0], b = r[1], e = r[2], g = r[3];
+        nd.zmin = r[4];
+        nd.zmax = r[5];
+        nd.zbar = r[6] / (double)(nd.end - nd.begin);
         if (b - a < min_ext) { double c = 0.5 * (a + b); a = c - 0.5 * min_ext; b = c + 0.5 * min_ext; }
         if (g - e < min_ext) { double c = 0.5 * (e + g); e = c - 0.5 * min_ext; g = c + 0.5 * min_ext; }
         nd.rect[0] = a; nd.rect[1] = b; nd.rect[2] = e; nd.rect[3] = g;
-    });
+    }
 
     // ---- sampling grids: a uniform lattice in (u, v, n) per non-root node
     // (Sec. IV-A), covering the image of D plus a margin, with per-axis density

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_functions():
     txt = open(os.path.join(ROOT, "include", "hhffbp.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", txt, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:long\s+long|\w+)\s*\*?\s*(\w+)\s*\(", txt, flags=re.M)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -197,3 +197,12 @@ def test_wrappers_refuse_wrong_buffers_before_any_cuda_call():
     plan = hh.Plan(s.traj, s.freqs, s.grid, host_only=True, leaf_size=16)
     with pytest.raises(ValueError, match="elements"):
         plan.form_image(echo, out=torch.zeros(7, dtype=torch.complex64))
+
+
+def test_mufu_probe_refuses_bad_arguments():
+    """Argument checks come before any CUDA call, so they hold without a device."""
+    L = hh.lib()
+    ops, ms = ctypes.c_int64(0), ctypes.c_float(0)
+    assert L.hh_mufu_throughput(7, 16, None, ctypes.byref(ops), ctypes.byref(ms)) == hh.HH_ERR_ARG
+    assert L.hh_mufu_throughput(0, 0, None, ctypes.byref(ops), ctypes.byref(ms)) == hh.HH_ERR_ARG
+    assert L.hh_mufu_throughput(0, 16, None, None, ctypes.byref(ms)) == hh.HH_ERR_ARG

@@ -56,10 +56,11 @@ PAPER_SIM1 = {"speedup_hhffbpa_vs_bpa": 62.09, "psnr_hhffbpa_vs_bpa_db": 45.98,
 
 # DRAM bytes (read + write) per evaluated sample of a stage's kernel, from an ncu capture of
 # one launch on the mid workload in its benchmark plan (leaf 1024, eta 1.5: the large
-# workload's leaf size; dram__bytes_read.sum + dram__bytes_write.sum = 44.8 MB + 49.8 MB for
+# workload's leaf size; dram__bytes_read.sum + dram__bytes_write.sum = 44.7 MB + 45.3 MB for
 # 5,713,647 evaluated leaf samples; profiles/k_stage0_mid.md), scaled to a launch by the
 # samples it evaluates; keyed by the kernel revision, null for other kernels.
-TRAFFIC_PER_SAMPLE = {("leaf_subimages", "paired two-sample loop, tile table"): (44828928 + 49848832) / 5713647}
+TRAFFIC_PER_SAMPLE = {("leaf_subimages", "paired two-sample loop, tile table, floor(256/npair) member groups"):
+                      (44679936 + 45312512) / 5713647}
 STAGE0_REVISION = "paired two-sample loop, tile table, floor(256/npair) member groups"
 
 # Algorithmic work per unit: a BPA-type update (one position at one point) takes one

@@ -501,8 +501,11 @@ int hhffbp_form_image(const hh_plan* cp, const void* echo_c64, void* image_c64, 
     HH_MARK(HH_STAGE_RC, -1);
     HH_CUDA(cudaMemsetAsync(p->d_counters, 0, sizeof(int64_t) * hh::CNT_N, s));
     const hh::KConst kc = hh::make_kconst(p);
+    // the factorised forward reads P-only rows (windows, fallbacks); the (P, dP) pair rows serve
+    // a single-level plan's direct BPA and the gradient
     HH_LAUNCH(hh::launch_rc(echo, static_cast<const int64_t*>(p->d_perm), p->n_pos, p->n_f, p->n_fft, p->gate0,
-                            p->gate_n, p->d_twiddle, p->d_prof, p->d_prof2, cuda_stream));
+                            p->gate_n, p->d_twiddle, p->n_levels == 1 ? p->d_prof : nullptr, p->d_prof2,
+                            cuda_stream));
     if (p->n_levels > 1) {
         // top-down: which lattice samples the image needs (the footprints of needed points)
         HH_MARK(HH_STAGE_NEED_FINAL, p->n_levels - 1);

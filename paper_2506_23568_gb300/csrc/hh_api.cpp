@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <unordered_map>
@@ -199,20 +200,38 @@ std::vector<hh::DNode> device_nodes(const hh_plan* p) {
 
 // Member positions in tree order (FP64) and, per non-root level, each member relative to the
 // centre of its node: v = centre - p' and |v|^2 / 2 (FP32), level-major.
-void member_arrays(const hh_plan* p, const std::vector<hh::DNode>& dn, std::vector<double>& mem_pos,
-                   std::vector<float>& nodev) {
+// Entries of the two member arrays: positions in tree order (3 doubles each) and, per level
+// below the root, every member relative to its node's centre with |v|^2 / 2 (4 floats).
+size_t n_mem_pos(const hh_plan* p) { return 3 * (size_t)p->n_pos; }
+size_t n_nodev(const hh_plan* p) { return 4 * (size_t)p->n_pos * (size_t)std::max(1, p->n_levels - 1); }
+
+// Process-wide host staging of the member arrays, reused by every plan (no zero fill and no
+// fresh pages per plan).  A cudaMemcpyAsync from pageable memory returns once its source has
+// been copied out, so the buffers are free again after the uploads; the mutex serialises
+// their users.
+struct MemberStage {
+    std::mutex mu;
+    std::unique_ptr<double[]> pos;
+    std::unique_ptr<float[]> vec;
+    size_t pos_cap = 0, vec_cap = 0;
+};
+MemberStage& member_stage() {
+    static MemberStage m;
+    return m;
+}
+
+// Fills mem_pos [n_mem_pos] and nodev [n_nodev] (every entry).
+void member_arrays(const hh_plan* p, const std::vector<hh::DNode>& dn, double* mem_pos, float* nodev) {
     const int64_t n_pos = p->n_pos;
-    mem_pos.assign(3 * (size_t)n_pos, 0.0);
     const int64_t blk = 4096;  // positions in tree order, gathered in blocks
     hh::parallel_for((n_pos + blk - 1) / blk, n_pos >= 32768 ? 16 : 1, [&](int64_t b) {
         for (int64_t q = b * blk; q < std::min(n_pos, (b + 1) * blk); ++q)
             for (int k = 0; k < 3; ++k) mem_pos[3 * q + k] = p->traj[3 * p->perm[q] + k];
     });
-    const int n_vec_levels = std::max(1, p->n_levels - 1);
-    nodev.assign(4 * (size_t)n_pos * (size_t)n_vec_levels, 0.f);
+    if (p->n_levels < 2) std::fill(nodev, nodev + n_nodev(p), 0.f);  // no level below a root leaf
     const int64_t n_vec_nodes = p->n_levels > 1 ? p->level_start[p->n_levels - 1] : 0;
     hh::parallel_for(n_vec_nodes, n_pos >= 32768 ? 16 : 1, [&](int64_t j) {  // nodes of levels 0 .. L-2
-        float* out_l = nodev.data() + 4 * (size_t)n_pos * (size_t)p->nodes[j].level;
+        float* out_l = nodev + 4 * (size_t)n_pos * (size_t)p->nodes[j].level;
         const hh::DNode& L = dn[j];
         for (int64_t q = L.mem_begin; q < L.mem_end; ++q) {
             const float vx = (float)(L.cx - mem_pos[3 * q]), vy = (float)(L.cy - mem_pos[3 * q + 1]),
@@ -228,6 +247,26 @@ void member_arrays(const hh_plan* p, const std::vector<hh::DNode>& dn, std::vect
 int upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     HH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
     return HH_OK;
+}
+
+// Member arrays of plan p, computed into the shared staging buffers and copied to the plan's
+// device arrays on stream s.
+int upload_member_arrays(const hh_plan* p, const std::vector<hh::DNode>& dn, cudaStream_t s) {
+    MemberStage& ms = member_stage();
+    std::lock_guard<std::mutex> lk(ms.mu);
+    const size_t np = n_mem_pos(p), nv = n_nodev(p);
+    if (ms.pos_cap < np) {
+        ms.pos.reset(new (std::nothrow) double[np]);
+        ms.pos_cap = ms.pos ? np : 0;
+    }
+    if (ms.vec_cap < nv) {
+        ms.vec.reset(new (std::nothrow) float[nv]);
+        ms.vec_cap = ms.vec ? nv : 0;
+    }
+    if (!ms.pos || !ms.vec) return HH_ERR_OOM;
+    member_arrays(p, dn, ms.pos.get(), ms.vec.get());
+    if (int r = upload(p->d_mem_pos, ms.pos.get(), sizeof(double) * np, s)) return r;
+    return upload(p->d_nodev, ms.vec.get(), sizeof(float) * nv, s);
 }
 
 #define HH_TRY(expr)            \
@@ -311,16 +350,13 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         return HH_ERR_CUDA;
     }
     std::vector<hh::DNode> dn = device_nodes(p);
-    std::vector<double> mem_pos;
-    std::vector<float> nodev;
-    member_arrays(p, dn, mem_pos, nodev);
     std::vector<float> tw = hh::twiddle_table(p->n_fft);
     const int64_t n_vox = (int64_t)grid->nx * grid->ny * grid->nz;
     HH_TRY(dev_alloc(p, &p->d_nodes, sizeof(hh::DNode) * dn.size()));
     HH_TRY(dev_alloc(p, &p->d_tile_off, sizeof(int64_t) * p->tile_off.size()));
-    HH_TRY(dev_alloc(p, &p->d_mem_pos, sizeof(double) * mem_pos.size()));
+    HH_TRY(dev_alloc(p, &p->d_mem_pos, sizeof(double) * n_mem_pos(p)));
     HH_TRY(dev_alloc(p, &p->d_perm, sizeof(int64_t) * n_pos));
-    HH_TRY(dev_alloc(p, &p->d_nodev, sizeof(float) * nodev.size()));
+    HH_TRY(dev_alloc(p, &p->d_nodev, sizeof(float) * n_nodev(p)));
     HH_TRY(dev_alloc(p, &p->d_prof, 16 * (size_t)n_pos * (size_t)p->gate_n));
     HH_TRY(dev_alloc(p, &p->d_prof2, 8 * (size_t)n_pos * (size_t)((p->gate_n + 2) & ~(int64_t)1)));
     if (p->max_pool > 0) {
@@ -373,9 +409,8 @@ int hhffbp_plan(const double* traj_xyz, int64_t n_pos, const double* freqs_hz, i
         HH_TRY(upload(p->d_tile_off, p->tile_off.data(), sizeof(int64_t) * p->tile_off.size(), s));
     if (p->d_pair_off)
         HH_TRY(upload(p->d_pair_off, p->pair_off.data(), sizeof(int64_t) * p->pair_off.size(), s));
-    HH_TRY(upload(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), s));
+    HH_TRY(upload_member_arrays(p, dn, s));
     HH_TRY(upload(p->d_perm, p->perm.data(), sizeof(int64_t) * n_pos, s));
-    HH_TRY(upload(p->d_nodev, nodev.data(), sizeof(float) * nodev.size(), s));
     HH_TRY(upload(p->d_twiddle, tw.data(), sizeof(float) * tw.size(), s));
     if (p->d_tiles) {
         const int te = hh::launch_tile_table(p, cuda_stream);
@@ -404,12 +439,8 @@ int hhffbp_plan_update_positions(hh_plan* p, const double* traj_xyz, void* cuda_
     p->traj.assign(traj_xyz, traj_xyz + 3 * p->n_pos);
     if (!p->on_device) return HH_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-    std::vector<double> mem_pos;
-    std::vector<float> nodev;
-    member_arrays(p, device_nodes(p), mem_pos, nodev);
-    HH_CUDA(cudaMemcpyAsync(p->d_mem_pos, mem_pos.data(), sizeof(double) * mem_pos.size(), cudaMemcpyHostToDevice, s));
-    HH_CUDA(cudaMemcpyAsync(p->d_nodev, nodev.data(), sizeof(float) * nodev.size(), cudaMemcpyHostToDevice, s));
-    HH_CUDA(cudaStreamSynchronize(s));  // the host arrays are released on return
+    if (int r = upload_member_arrays(p, device_nodes(p), s)) return r;
+    HH_CUDA(cudaStreamSynchronize(s));  // the new positions are in place on return
     p->last_stream = cuda_stream;
     return HH_OK;
 }

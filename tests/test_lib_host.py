@@ -206,3 +206,34 @@ def test_mufu_probe_refuses_bad_arguments():
     assert L.hh_mufu_throughput(7, 16, None, ctypes.byref(ops), ctypes.byref(ms)) == hh.HH_ERR_ARG
     assert L.hh_mufu_throughput(0, 0, None, ctypes.byref(ops), ctypes.byref(ms)) == hh.HH_ERR_ARG
     assert L.hh_mufu_throughput(0, 16, None, None, ctypes.byref(ms)) == hh.HH_ERR_ARG
+
+
+def _raster(nx_pos, ny_pos, pitch=0.004, z=0.0):
+    """A regular raster of positions: every x value repeats across the rows (and every y value
+    along a row), so that the k-d split's (coordinate, index) order is decided by the index
+    inside runs of equal coordinates."""
+    xs, ys = np.meshgrid(np.arange(nx_pos) * pitch, np.arange(ny_pos) * pitch, indexing="ij")
+    return np.column_stack([xs.ravel() - xs.mean(), ys.ravel() - ys.mean(), np.full(xs.size, z)])
+
+
+@pytest.mark.parametrize("shape,leaf", [((64, 64), 16), ((48, 40), 15), ((128, 96), 64)])
+def test_host_plan_equals_oracle_plan_with_tied_coordinates(shape, leaf):
+    """Runs of equal x (and y) coordinates straddle the split points: the bucket selection of
+    the library's split must give exactly the oracle's halves."""
+    s = synth.small()
+    traj = _raster(*shape)
+    ge = hh.Plan(traj, s.freqs, s.grid, host_only=True, leaf_size=leaf).export()
+    oe = oracle.Plan(traj, s.freqs, s.grid, leaf_size=leaf).export()
+    assert ge["n_levels"] == oe["n_levels"] and ge["depth_leaves"] == oe["depth_leaves"]
+    _compare_plans(ge, oe)
+
+
+def test_host_plan_equals_oracle_plan_on_a_line():
+    """All positions share one x coordinate (a line along y): the splits along x fall back to
+    ordering by index alone."""
+    s = synth.small()
+    n = 3000
+    traj = np.column_stack([np.zeros(n), np.linspace(-0.06, 0.06, n), np.zeros(n)])
+    ge = hh.Plan(traj, s.freqs, s.grid, host_only=True, leaf_size=20).export()
+    oe = oracle.Plan(traj, s.freqs, s.grid, leaf_size=20).export()
+    _compare_plans(ge, oe)

@@ -237,3 +237,31 @@ def test_host_plan_equals_oracle_plan_on_a_line():
     ge = hh.Plan(traj, s.freqs, s.grid, host_only=True, leaf_size=20).export()
     oe = oracle.Plan(traj, s.freqs, s.grid, leaf_size=20).export()
     _compare_plans(ge, oe)
+
+
+def test_host_plans_built_concurrently_equal_one_built_alone():
+    """Plans built at once from several host threads (the C call releases the interpreter
+    lock) share the library's worker pool, which serves one loop at a time; the others run
+    their loops on threads of their own. Every plan must equal the one built alone."""
+    import threading
+
+    s = synth.CONFIGS["mid"]()
+    ref = hh.Plan(s.traj, s.freqs, s.grid, host_only=True, leaf_size=256).export()
+    out = [None] * 4
+
+    def build(i):
+        out[i] = hh.Plan(s.traj, s.freqs, s.grid, host_only=True, leaf_size=256).export()
+
+    threads = [threading.Thread(target=build, args=(i,)) for i in range(len(out))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for e in out:
+        for k in ["begin", "end", "N", "child0", "nchild"]:
+            np.testing.assert_array_equal(e[k], ref[k], err_msg=k)
+        np.testing.assert_array_equal(e["rect"], ref["rect"])
+        np.testing.assert_array_equal(e["lo"], ref["lo"])
+        ls = ref["level_start"]
+        for k in range(ls[0], ls[-2]):
+            assert set(e["perm"][e["begin"][k]:e["end"][k]]) == set(ref["perm"][ref["begin"][k]:ref["end"][k]])

@@ -15,8 +15,10 @@
  *   - Complex arrays are interleaved (re, im) doubles.
  *   - Images/voxel lists are float64[n][3] points; the caller orders them.
  *
- * Parity notes: functions marked "parity unpinned" have no value printed in the
- * paper to compare against; they are pinned only by invariants and limits.
+ * Parity notes: the paper prints no value for these functions to compare against.
+ * Each is pinned by something other than itself -- a closed form, an invariant, a
+ * special case that reduces to a textbook routine, or brute force on tiny inputs --
+ * in the CPU tests; none is "parity unpinned".
  */
 #define _POSIX_C_SOURCE 199309L
 #include <math.h>
